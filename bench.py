@@ -1,0 +1,393 @@
+"""Benchmark of the quaternion GEMM hot path on GB300.
+
+One step = one call of the C-ABI qgemm() on the benchmark workload:
+FP64 quaternion GEMM, m = n = k = 4096, op (N, N), interleaved column-major,
+alpha and beta random unit quaternions, components iid N(0,1) (the square
+sweep of the FP64 path at its target size).  The metric is effective FLOP/s,
+32 m n k real flops per QGEMM.  Inputs (1.5 GiB) are larger than the 126 MB
+L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  Under torchrun each rank runs an independent
+replica of the workload on its own GPU (the path does not shard); value is
+the sum of all ranks' work over the slowest rank's time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QGEMM FLOP/s (32*m*n*k), FP64 DMMA path"
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "fp64_qgemm_kernel_4096_NN_interleaved.txt")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_1903_05575_gb300", "csrc", "fp64_dmma.cu")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--size", type=int, default=4096)
+    p.add_argument("--layout", default="interleaved", choices=["interleaved", "planes"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload_config(args):
+    n = args.size
+    return {"workload": "fp64 qgemm m=n=k=%d op=NN %s alpha,beta unit quaternions N(0,1)"
+                        % (n, args.layout),
+            "m": n, "n": n, "k": n, "opA": "N", "opB": "N", "layout": args.layout,
+            "precision": "fp64",
+            "l2": "inputs %.2f GiB > 126 MB L2; no flush" % (3 * n * n * 32 / 2**30)}
+
+
+# ------------------------------------------------------------- clocks ---
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), float(f[3]) if f[3] not in ("[N/A]", "N/A") else 0.0,
+                             f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [r for r in rows if r[2] > 0.3 * max(x[2] for x in rows)] or rows
+        reasons = set()
+        for r in load:
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                "sw_power_cap"), r[3:]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in load),
+                "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows),
+                "samples": len(load), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------ cpu baseline ---
+def oracle_baseline(n, target_s=12.0, layout="interleaved"):
+    """The FP64 oracle, as it stands, on this host's cores: a bounded sample of
+    the workload (all m rows, k terms, a few columns of C), scaled to the
+    metric's unit."""
+    import numpy as np
+
+    import qsynth
+    from oracle import oracle as orc
+    m = k = n
+    A = qsynth.normal(m, k, 1906, layout)
+    alpha, beta = qsynth.unit_quaternion(1907), qsynth.unit_quaternion(1908)
+    cores = orc.max_threads()
+
+    def run(cols):
+        B = qsynth.normal(k, cols, 1909, layout)
+        C = qsynth.normal(m, cols, 1910, layout)
+        t0 = time.perf_counter()
+        orc.qgemm("N", "N", m, cols, k, alpha, A, B, beta, C, layout=layout)
+        return time.perf_counter() - t0
+
+    cols = max(1, cores)
+    t = run(cols)
+    want = int(cols * target_s / max(t, 1e-3))
+    cols2 = max(cols, min(want, n))
+    if cols2 > cols:
+        t = run(cols2)
+        cols = cols2
+    flops = 32.0 * m * cols * k
+    return {"value": flops / t / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": "fp64 oracle on %d x %d x %d (all rows and k of the workload, %d of %d "
+                      "columns of C), %.1f s" % (m, cols, k, cols, n, t),
+            "seconds": t}
+
+
+# ------------------------------------------------------------ helpers ---
+def profiled_traffic():
+    """DRAM bytes per launch of the benchmarked kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    try:
+        lines = open(PROFILE_SUMMARY).read().splitlines()
+        src_hash = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    vals = {}
+    for line in lines:
+        if "=" in line and line.startswith("bench:"):
+            key, val = line[len("bench:"):].split("=", 1)
+            vals[key.strip()] = val.strip()
+    if vals.get("kernel_source_sha256_16") != src_hash:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# -------------------------------------------------------------- impls ---
+def run_reference(args):
+    """The oracle as the reference arm: each step is a bounded sample of the
+    workload on the host cores (rank 0 only)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = args.size
+    per_step = max(2.0, 100.0 / max(1, args.steps + args.warmup))
+    cfg = workload_config(args)
+    import qsynth
+    from oracle import oracle as orc
+    A = qsynth.normal(n, n, 1906, args.layout)
+    alpha, beta = qsynth.unit_quaternion(1907), qsynth.unit_quaternion(1908)
+    cores = orc.max_threads()
+    cols = max(1, cores)
+    B = qsynth.normal(n, n, 1909, args.layout)
+    C0 = qsynth.normal(n, n, 1910, args.layout)
+
+    def step(c):
+        Bs = B[:c].copy() if args.layout == "interleaved" else B[:, :c].copy()
+        Cs = C0[:c].copy() if args.layout == "interleaved" else C0[:, :c].copy()
+        t0 = time.perf_counter()
+        orc.qgemm("N", "N", n, c, n, alpha, A, Bs, beta, Cs, layout=args.layout)
+        return time.perf_counter() - t0
+
+    t = step(cols)
+    cols = max(1, min(n, int(cols * per_step / max(t, 1e-3))))
+    for _ in range(args.warmup):
+        step(cols)
+    times = [step(cols) for _ in range(args.steps)]
+    tt = sum(times)
+    value = 32.0 * n * cols * n * len(times) / tt / 1e12
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tt / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": "each step: fp64 oracle on %d x %d x %d (%d of %d columns "
+                                       "of C)" % (n, cols, n, cols, n)},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1903_05575_gb300 import _abi, ops
+
+    world, rank, local = dist_setup(args)
+    n = args.size
+    m = k = n
+    layout = args.layout
+    dev = torch.device("cuda", torch.cuda.current_device())
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1903 + rank)
+    if layout == "interleaved":
+        shape = (n, n, 4)
+    else:
+        shape = (4, n, n)
+    A = torch.randn(shape, dtype=torch.float64, device=dev, generator=gen)
+    B = torch.randn(shape, dtype=torch.float64, device=dev, generator=gen)
+    C = torch.randn(shape, dtype=torch.float64, device=dev, generator=gen)
+    import qsynth
+    alpha, beta = qsynth.unit_quaternion(1911), qsynth.unit_quaternion(1912)
+    stream = torch.cuda.current_stream()
+    L = _abi.lib()
+    lda, psA, _ = ops.geometry(A, layout)
+    al, be = _abi.q4(alpha), _abi.q4(beta)
+
+    def step():
+        rc = L.qgemm(0, 0, m, n, k, al, A.data_ptr(), lda, psA, B.data_ptr(), lda, psA, be,
+                     C.data_ptr(), lda, psA, _abi.LAYOUT[layout], 0, None, 0, stream.cuda_stream)
+        if rc != 0:
+            raise _abi.QgemmError(rc)
+
+    # live peak of the FP64 tensor pipe (MEASURED_PEAKS.json has no FP64 figure)
+    dmma_peak = ops.probe_peak(0, 0.4)
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier(world)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = max_over_ranks(world, ms)
+    flops_step = 32.0 * m * n * k
+    value = flops_step * world / (ms_max * 1e-3) / 1e12
+    kernel_ms = ms  # one kernel launch per step
+    achieved = flops_step / (kernel_ms * 1e-3) / 1e12
+    rc = L.qgemm_get_last_device_error()
+    if rc != 0:
+        raise _abi.QgemmError(rc, "device status after timing")
+
+    # end to end: pinned host buffers, H2D of A, B, C, the call, D2H of C
+    e2e = None
+    if not args.no_e2e:
+        hA = A.cpu().pin_memory()
+        hB = B.cpu().pin_memory()
+        hC = C.cpu().pin_memory()
+        hOut = torch.empty_like(hC).pin_memory()
+        bytes_in = 3 * hA.numel() * 8
+        bytes_out = hC.numel() * 8
+        steps_e2e = max(2, args.steps)
+
+        def e2e_step():
+            A.copy_(hA, non_blocking=True)
+            B.copy_(hB, non_blocking=True)
+            C.copy_(hC, non_blocking=True)
+            step()
+            hOut.copy_(C, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(steps_e2e):
+            e2e_step()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = max_over_ranks(world, f0.elapsed_time(f1) / steps_e2e)
+        e2e = {"value": flops_step * world / (ms_e2e * 1e-3) / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": bytes_in, "d2h_bytes_per_step": bytes_out,
+               "ms_per_step": ms_e2e}
+
+    # error of one benchmarked result against the oracle, on sampled entries
+    err = None
+    if rank == 0:
+        from oracle import oracle as orc
+        A_h, B_h = A.cpu().numpy(), B.cpu().numpy()
+        C_h = torch.randn(shape, dtype=torch.float64, generator=torch.Generator().manual_seed(5)).numpy()
+        C.copy_(torch.from_numpy(C_h))
+        step()
+        got = C.cpu().numpy()
+        g = np.random.default_rng(7)
+        rows, cols = g.integers(0, m, 512), g.integers(0, n, 512)
+        ref = orc.qgemm_entries("N", "N", m, n, k, alpha, A_h, B_h, beta, C_h, rows, cols,
+                                layout=layout)
+        import qsynth as qs
+        G = qs.components(got, m, layout)[rows, cols]
+        err = float(np.linalg.norm(G - ref) / np.linalg.norm(ref))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_baseline(n, layout=layout)
+
+    if rank != 0:
+        return
+    traffic = profiled_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(args),
+        "rel_err_sampled": err, "tolerance": 1e-12,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": dmma_peak,
+                     "unit": "TFLOP/s", "frac": achieved / dmma_peak, "traffic": traffic,
+                     "kernel": "fp64_qgemm_kernel",
+                     "peak_source": "FP64 tensor pipe (DMMA m16n8k4) measured live by "
+                                    "qgemm_probe_peak(0); MEASURED_PEAKS.json has no FP64 entry"},
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,220 @@
+/*
+ * qgemm.h -- C ABI of the GB300 quaternion GEMM library.
+ *
+ * The operation (Sec. 3.1, Eq. general_gemm, over the quaternions H):
+ *
+ *     C <- alpha * op(A) * op(B) + beta * C
+ *
+ *   - A quaternion is q = q^0 e0 + q^1 e1 + q^2 e2 + q^3 e3 (Sec. 2.1,
+ *     Eq. quaternion_def); products are Hamilton products (Eq. quaternion_prod),
+ *     taken in the order A_{i kappa} B_{kappa j}.
+ *   - op(X) is X (N), X^T (T), conj(X) (C) or X^H = conj(X)^T (H), with the
+ *     element-wise conjugate and conjugate transpose of Sec. 2.2.
+ *   - alpha and beta multiply from the LEFT, (alpha P)_{ij} = alpha P_{ij}
+ *     (Sec. 2.2, Eq. no_scalar_comm_mat; Sec. 3.1, Algorithm 2 folds alpha into
+ *     the packed A block).  Quaternions do not commute, so this is observable.
+ *   - op(A) is m x k, op(B) is k x n, C is m x n.  The STORED A is m x k for N/C
+ *     and k x m for T/H (likewise B).
+ *
+ * Storage (column-major, Sec. 3.1): element (r, c) of a stored matrix with
+ * leading dimension ld (in quaternion elements) sits at r + c*ld.
+ *   QGEMM_INTERLEAVED:  the four components of an element are contiguous,
+ *       [q^0, q^1, q^2, q^3] (Sec. 4): component s at 4*(r + c*ld) + s reals.
+ *   QGEMM_SPLIT_PLANES: four real column-major planes Q^s (Sec. 2.2,
+ *       Eq. quaternion_mat_def): component s at s*plane_stride + r + c*ld reals.
+ *       plane_stride must be >= ld * (stored columns); it is ignored for the
+ *       interleaved layout.
+ *
+ * Precision:
+ *   QGEMM_FP64:            double data; products on FP64 tensor cores (DMMA),
+ *                          FP64 accumulation and epilogue.
+ *   QGEMM_FP32_SPLIT_BF16: float data; each operand is split into three BF16
+ *                          terms (hi, mid, lo), the six leading term products
+ *                          run on the BF16 tensor cores (tcgen05) with FP32
+ *                          accumulation in tensor memory, drained in K-chunks
+ *                          into a higher-precision accumulator; alpha and beta
+ *                          are applied in FP64 and the result is rounded once
+ *                          to float.  Needs a workspace (qgemm_workspace_bytes).
+ *
+ * Memory and streams: every matrix pointer is a DEVICE pointer owned by the
+ * caller; alpha and beta are HOST arrays of 4 doubles, read during the call
+ * (so a captured CUDA graph freezes their values).  Calls are asynchronous on
+ * `stream` (a cudaStream_t; NULL is the legacy default stream): buffers must
+ * stay valid until the stream reaches the call.  The library never allocates
+ * device memory in these calls; scratch space is the caller's workspace.
+ * Elements must be aligned to their type (8 bytes FP64, 4 bytes FP32); tiles
+ * are fetched with the tensor memory accelerator when base and strides are
+ * 16-byte aligned, and with plain loads otherwise.
+ *
+ * Return values: 0 on success; -i when argument i (1-based) is invalid, in
+ * the manner of LAPACK's INFO; a positive QGEMM_ERR_* code otherwise.
+ * Argument checks happen before anything is launched.  A kernel that gives up
+ * on a bounded wait records QGEMM_ERR_TIMEOUT in a device status word that
+ * qgemm_get_last_device_error() reads.  The library never aborts, never
+ * prints, and has no CPU fallback: without a usable sm_103 device the calls
+ * return QGEMM_ERR_NO_DEVICE.
+ *
+ * BLAS conventions where the paper is silent: m == 0 or n == 0 returns at
+ * once; k == 0 or alpha == 0 gives C <- beta * C; beta == 0 means C is not
+ * read (it may hold NaN).
+ */
+#ifndef QGEMM_H
+#define QGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QGEMM_OP_N 0
+#define QGEMM_OP_T 1
+#define QGEMM_OP_C 2
+#define QGEMM_OP_H 3
+
+#define QGEMM_INTERLEAVED 0
+#define QGEMM_SPLIT_PLANES 1
+
+#define QGEMM_FP64 0
+#define QGEMM_FP32_SPLIT_BF16 1
+
+#define QGEMM_SUCCESS 0
+#define QGEMM_ERR_UNSUPPORTED 1 /* valid arguments, combination not implemented   */
+#define QGEMM_ERR_CUDA 2        /* a CUDA runtime call or launch failed            */
+#define QGEMM_ERR_TIMEOUT 3     /* a device-side bounded wait gave up              */
+#define QGEMM_ERR_NO_DEVICE 4   /* no usable sm_103 device / driver entry point    */
+#define QGEMM_ERR_WORKSPACE 5   /* workspace missing, too small or misaligned      */
+
+/*
+ * qgemm: C <- alpha op(A) op(B) + beta C   (Sec. 3.1, Eq. general_gemm).
+ *
+ *   1 opA, 2 opB         QGEMM_OP_{N,T,C,H}
+ *   3 m, 4 n, 5 k        sizes in quaternions, >= 0
+ *   6 alpha              host double[4], left scalar
+ *   7 A, 8 lda, 9 psA    device pointer, leading dim (>= max(1, stored rows)),
+ *                        plane stride (split planes only)
+ *  10 B, 11 ldb, 12 psB  likewise
+ *  13 beta               host double[4], left scalar
+ *  14 C, 15 ldc, 16 psC  device pointer (read unless beta == 0, then written)
+ *  17 layout             QGEMM_INTERLEAVED or QGEMM_SPLIT_PLANES (all three
+ *                        matrices share it)
+ *  18 precision          QGEMM_FP64 or QGEMM_FP32_SPLIT_BF16
+ *  19 workspace          device scratch, 256-byte aligned, or NULL if
+ *  20 workspace_bytes    qgemm_workspace_bytes() is 0
+ *  21 stream             cudaStream_t
+ */
+int qgemm(int opA, int opB, int64_t m, int64_t n, int64_t k,
+          const double alpha[4],
+          const void *A, int64_t lda, int64_t psA,
+          const void *B, int64_t ldb, int64_t psB,
+          const double beta[4],
+          void *C, int64_t ldc, int64_t psC,
+          int layout, int precision,
+          void *workspace, size_t workspace_bytes,
+          void *stream);
+
+/* Workspace qgemm() needs for these arguments (0 for QGEMM_FP64).  Returns 0
+ * for invalid arguments as well; qgemm() itself reports those. */
+size_t qgemm_workspace_bytes(int opA, int opB, int64_t m, int64_t n, int64_t k,
+                             int layout, int precision);
+
+/*
+ * One problem of a grouped batch (host struct).  Same meaning as the qgemm()
+ * arguments of the same names; ops are QGEMM_OP_* values.
+ */
+typedef struct qgemm_problem {
+    int32_t opA, opB;
+    int64_t m, n, k;
+    double alpha[4], beta[4];
+    const void *A; int64_t lda, psA;
+    const void *B; int64_t ldb, psB;
+    void *C; int64_t ldc, psC;
+} qgemm_problem;
+
+/*
+ * qgemm_batched_grouped: `count` independent problems in one persistent
+ * launch.  `problems` is a HOST array; it is validated, turned into a device
+ * tile schedule inside `workspace` (copied with cudaMemcpyAsync on `stream`),
+ * and the grouped kernel is launched.  Returns -(1000*p + i) when argument i
+ * of problem p is invalid (i numbered as in qgemm()), -1/-2 for problems /
+ * count, and -(3..7) for the trailing arguments.
+ */
+int qgemm_batched_grouped(const qgemm_problem *problems, int64_t count,
+                          int layout, int precision,
+                          void *workspace, size_t workspace_bytes,
+                          void *stream);
+
+/* Workspace for qgemm_batched_grouped() with these problems. */
+size_t qgemm_grouped_workspace_bytes(const qgemm_problem *problems, int64_t count,
+                                     int layout, int precision);
+
+/*
+ * Split form for CUDA-graph capture: qgemm_grouped_prepare() validates the
+ * problems and writes the schedule into `workspace` (asynchronous copy on
+ * `stream`); qgemm_grouped_launch() only launches the persistent kernel(s)
+ * that read it, so it can be captured and replayed.  The workspace must not
+ * be modified between the two.
+ */
+int qgemm_grouped_prepare(const qgemm_problem *problems, int64_t count,
+                          int layout, int precision,
+                          void *workspace, size_t workspace_bytes, void *stream);
+int qgemm_grouped_launch(void *workspace, void *stream);
+
+/*
+ * qgemm_backward: gradients of a quaternion linear map Y = X W, with
+ * X (mb x k), W (k x n), Y (mb x n) stored untransposed.  With the real inner
+ * product <P, Q> = Re tr(P^H Q) = sum of component products, and
+ * Re tr(PQ) = Re tr(QP) on H, a real loss L with componentwise gradient
+ * dY = dL/dY has
+ *     dX = dY W^H   (mb x k)      dW = X^H dY   (k x n)
+ * (conjugate transpose of Sec. 2.2, read directly by the tile loads; no
+ * transposed copy is made).  dX or dW may be NULL to skip that gradient.
+ * accumulate != 0 adds into dX / dW (beta = 1), else overwrites (beta = 0).
+ * Arguments are numbered 1..24 for the -i return in the order below.
+ */
+int qgemm_backward(int64_t mb, int64_t k, int64_t n,
+                   const void *X, int64_t ldx, int64_t psx,
+                   const void *W, int64_t ldw, int64_t psw,
+                   const void *dY, int64_t lddy, int64_t psdy,
+                   void *dX, int64_t lddx, int64_t psdx,
+                   void *dW, int64_t lddw, int64_t psdw,
+                   int accumulate, int layout, int precision,
+                   void *workspace, size_t workspace_bytes, void *stream);
+
+/* Workspace qgemm_backward() needs (the larger of its two products). */
+size_t qgemm_backward_workspace_bytes(int64_t mb, int64_t k, int64_t n,
+                                      int layout, int precision);
+
+/* Reads and clears the device status word (synchronises the device).
+ * Returns QGEMM_SUCCESS or QGEMM_ERR_TIMEOUT. */
+int qgemm_get_last_device_error(void);
+
+/* Static description of a status code. */
+const char *qgemm_status_string(int status);
+
+/*
+ * Test hook for the bounded waits: launches one kernel that waits on a
+ * barrier nothing ever arrives on, with the given limit in nanoseconds.  The
+ * wait gives up, the kernel records QGEMM_ERR_TIMEOUT and returns, so the
+ * context stays usable.  Returns the launch status.
+ */
+int qgemm_debug_unsatisfied_wait(uint64_t limit_ns, void *stream);
+
+/*
+ * Throughput microbenchmarks of the device's arithmetic pipes (no paper
+ * counterpart; they supply the roofline denominators).  which:
+ *   0 FP64 tensor (DMMA m16n8k4)   1 FP64 FMA (DFMA)   2 FP32 FMA (FFMA)
+ *   3 BF16 tensor (tcgen05.mma kind::f16, 128x256x16, FP32 accumulate)
+ * Runs for roughly `seconds` and writes the achieved TFLOP/s (2 per FMA).
+ */
+int qgemm_probe_peak(int which, double seconds, double *tflops, void *stream);
+
+/* Library version string. */
+const char *qgemm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QGEMM_H */

@@ -1,0 +1,261 @@
+// C ABI entry points: argument validation (BLAS rules), quick returns and
+// dispatch to the kernels.  Nothing here computes on the host.
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "internal.h"
+
+namespace qg {
+
+namespace {
+
+bool is_zero4(const double q[4]) {
+  return q[0] == 0.0 && q[1] == 0.0 && q[2] == 0.0 && q[3] == 0.0;
+}
+
+// Checks one operand.  pos is the 1-based position of its pointer argument;
+// ld and plane stride follow it.  rows/cols are the stored extent.
+int check_operand(int pos, const void *p, int64_t ld, int64_t ps, int64_t rows, int64_t cols,
+                  bool referenced, int layout, size_t elem) {
+  if (ld < (rows > 1 ? rows : 1)) return -(pos + 1);
+  if (!referenced) return 0;
+  if (p == nullptr) return -pos;
+  if (reinterpret_cast<uintptr_t>(p) % elem != 0) return -pos;
+  if (layout == QGEMM_SPLIT_PLANES && cols > 0) {
+    // planes must not overlap: plane s spans [s*ps, s*ps + ld*cols)
+    if (ps < 0 || ps < ld * cols) return -(pos + 2);
+  }
+  return 0;
+}
+
+}  // namespace
+
+// Validates qgemm() arguments into a GemmDesc.  Positions as in qgemm.h.
+int validate_gemm(int opA, int opB, int64_t m, int64_t n, int64_t k, const double *alpha,
+                  const void *A, int64_t lda, int64_t psA, const void *B, int64_t ldb,
+                  int64_t psB, const double *beta, void *C, int64_t ldc, int64_t psC,
+                  int layout, int precision, GemmDesc *d) {
+  if (opA < 0 || opA > 3) return -1;
+  if (opB < 0 || opB > 3) return -2;
+  if (m < 0) return -3;
+  if (n < 0) return -4;
+  if (k < 0) return -5;
+  if (alpha == nullptr) return -6;
+  if (beta == nullptr) return -13;
+  if (layout != QGEMM_INTERLEAVED && layout != QGEMM_SPLIT_PLANES) return -17;
+  if (precision != QGEMM_FP64 && precision != QGEMM_FP32_SPLIT_BF16) return -18;
+  const size_t elem = precision == QGEMM_FP64 ? sizeof(double) : sizeof(float);
+  const bool alpha_zero = is_zero4(alpha);
+  const bool product = m > 0 && n > 0 && k > 0 && !alpha_zero;
+  const int64_t ra = op_trans(opA) ? k : m, ca = op_trans(opA) ? m : k;
+  const int64_t rb = op_trans(opB) ? n : k, cb = op_trans(opB) ? k : n;
+  int rc = check_operand(7, A, lda, psA, ra, ca, product, layout, elem);
+  if (rc) return rc;
+  rc = check_operand(10, B, ldb, psB, rb, cb, product, layout, elem);
+  if (rc) return rc;
+  rc = check_operand(14, C, ldc, psC, m, n, m > 0 && n > 0, layout, elem);
+  if (rc) return rc;
+  d->opA = opA;
+  d->opB = opB;
+  d->m = m;
+  d->n = n;
+  d->k = product ? k : 0;
+  std::memcpy(d->alpha, alpha, sizeof(d->alpha));
+  std::memcpy(d->beta, beta, sizeof(d->beta));
+  d->A = MatView{A, ra, ca, lda, psA};
+  d->B = MatView{B, rb, cb, ldb, psB};
+  d->C = C;
+  d->ldc = ldc;
+  d->psc = psC;
+  d->layout = layout;
+  d->beta_zero = is_zero4(beta);
+  return 0;
+}
+
+EncodeTiledFn encode_tiled_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+uint64_t wait_limit_ns() {
+  static uint64_t v = [] {
+    const char *s = std::getenv("QGEMM_WAIT_LIMIT_MS");
+    double ms = s ? std::atof(s) : 2000.0;
+    if (!(ms > 0.0)) ms = 2000.0;
+    return static_cast<uint64_t>(ms * 1e6);
+  }();
+  return v;
+}
+
+int device_ready() {
+  static int cache[64];  // 0 unknown, 1 ok, 2 unusable
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return QGEMM_ERR_NO_DEVICE;
+  }
+  if (dev < 0 || dev >= 64) return QGEMM_ERR_NO_DEVICE;
+  if (cache[dev] == 0) {
+    int major = 0, minor = 0;
+    bool ok = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) ==
+                  cudaSuccess &&
+              cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) ==
+                  cudaSuccess;
+    cudaGetLastError();
+    cache[dev] = (ok && major == 10 && minor == 3 && encode_tiled_fn() != nullptr) ? 1 : 2;
+  }
+  return cache[dev] == 1 ? QGEMM_SUCCESS : QGEMM_ERR_NO_DEVICE;
+}
+
+}  // namespace qg
+
+using namespace qg;
+
+extern "C" {
+
+int qgemm(int opA, int opB, int64_t m, int64_t n, int64_t k, const double alpha[4],
+          const void *A, int64_t lda, int64_t psA, const void *B, int64_t ldb, int64_t psB,
+          const double beta[4], void *C, int64_t ldc, int64_t psC, int layout, int precision,
+          void *workspace, size_t workspace_bytes, void *stream) {
+  GemmDesc d;
+  int rc = validate_gemm(opA, opB, m, n, k, alpha, A, lda, psA, B, ldb, psB, beta, C, ldc, psC,
+                         layout, precision, &d);
+  if (rc) return rc;
+  size_t need = 0;
+  if (precision == QGEMM_FP32_SPLIT_BF16 && d.k > 0) {
+    rc = split_workspace_bytes(d, &need);
+    if (rc) return rc;
+  }
+  if (need > 0) {
+    if (workspace == nullptr || reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return -19;
+    if (workspace_bytes < need) return -20;
+  }
+  if (m == 0 || n == 0) return QGEMM_SUCCESS;
+  rc = device_ready();
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (d.k == 0) return launch_scale(d, precision == QGEMM_FP64, s);
+  if (precision == QGEMM_FP64) return launch_fp64_gemm(d, s);
+  return launch_split_gemm(d, workspace, workspace_bytes, s);
+}
+
+size_t qgemm_workspace_bytes(int opA, int opB, int64_t m, int64_t n, int64_t k, int layout,
+                             int precision) {
+  if (precision != QGEMM_FP32_SPLIT_BF16) return 0;
+  if (opA < 0 || opA > 3 || opB < 0 || opB > 3 || m < 0 || n < 0 || k < 0) return 0;
+  if (layout != QGEMM_INTERLEAVED && layout != QGEMM_SPLIT_PLANES) return 0;
+  if (m == 0 || n == 0 || k == 0) return 0;
+  GemmDesc d{};
+  d.opA = opA;
+  d.opB = opB;
+  d.m = m;
+  d.n = n;
+  d.k = k;
+  d.layout = layout;
+  size_t b = 0;
+  if (split_workspace_bytes(d, &b)) return 0;
+  return b;
+}
+
+size_t qgemm_backward_workspace_bytes(int64_t mb, int64_t k, int64_t n, int layout,
+                                      int precision) {
+  size_t a = qgemm_workspace_bytes(QGEMM_OP_N, QGEMM_OP_H, mb, k, n, layout, precision);
+  size_t b = qgemm_workspace_bytes(QGEMM_OP_H, QGEMM_OP_N, k, n, mb, layout, precision);
+  return a > b ? a : b;
+}
+
+int qgemm_backward(int64_t mb, int64_t k, int64_t n, const void *X, int64_t ldx, int64_t psx,
+                   const void *W, int64_t ldw, int64_t psw, const void *dY, int64_t lddy,
+                   int64_t psdy, void *dX, int64_t lddx, int64_t psdx, void *dW, int64_t lddw,
+                   int64_t psdw, int accumulate, int layout, int precision, void *workspace,
+                   size_t workspace_bytes, void *stream) {
+  if (mb < 0) return -1;
+  if (k < 0) return -2;
+  if (n < 0) return -3;
+  if (layout != QGEMM_INTERLEAVED && layout != QGEMM_SPLIT_PLANES) return -20;
+  if (precision != QGEMM_FP64 && precision != QGEMM_FP32_SPLIT_BF16) return -21;
+  const double one[4] = {1.0, 0.0, 0.0, 0.0};
+  const double zero[4] = {0.0, 0.0, 0.0, 0.0};
+  const double *beta = accumulate ? one : zero;
+  // Map qgemm()'s -i positions back to this function's argument numbers.
+  auto remap = [](int rc, const int *map) -> int {
+    if (rc >= 0) return rc;
+    int pos = -rc;
+    return (pos >= 1 && pos <= 21 && map[pos]) ? -map[pos] : rc;
+  };
+  // dX = dY W^H : op(A) = dY (mb x n), op(B) = W^H (n x k), C = dX (mb x k)
+  static const int mapX[22] = {0, 0, 0, 1, 2, 3, 0, 10, 11, 12, 7, 8, 9, 0, 13, 14, 15, 20, 21,
+                               22, 23};
+  // dW = X^H dY : op(A) = X^H (k x mb), op(B) = dY (mb x n), C = dW (k x n)
+  static const int mapW[22] = {0, 0, 0, 2, 3, 1, 0, 4, 5, 6, 10, 11, 12, 0, 16, 17, 18, 20, 21,
+                               22, 23};
+  if (dX != nullptr) {
+    int rc = qgemm(QGEMM_OP_N, QGEMM_OP_H, mb, k, n, one, dY, lddy, psdy, W, ldw, psw, beta, dX,
+                   lddx, psdx, layout, precision, workspace, workspace_bytes, stream);
+    if (rc) return remap(rc, mapX);
+  }
+  if (dW != nullptr) {
+    int rc = qgemm(QGEMM_OP_H, QGEMM_OP_N, k, n, mb, one, X, ldx, psx, dY, lddy, psdy, beta, dW,
+                   lddw, psdw, layout, precision, workspace, workspace_bytes, stream);
+    if (rc) return remap(rc, mapW);
+  }
+  return QGEMM_SUCCESS;
+}
+
+int qgemm_get_last_device_error(void) {
+  if (device_ready() != QGEMM_SUCCESS) return QGEMM_ERR_NO_DEVICE;
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return QGEMM_ERR_CUDA;
+  }
+  int e = fp64_take_device_error();
+  int e2 = split_take_device_error();
+  int e3 = grouped_take_device_error();
+  int e4 = misc_take_device_error();
+  if (e) return e;
+  if (e2) return e2;
+  if (e3) return e3;
+  return e4;
+}
+
+const char *qgemm_status_string(int status) {
+  if (status < 0) return "invalid argument (-status is its 1-based position)";
+  switch (status) {
+    case QGEMM_SUCCESS: return "success";
+    case QGEMM_ERR_UNSUPPORTED: return "combination not supported";
+    case QGEMM_ERR_CUDA: return "CUDA runtime error";
+    case QGEMM_ERR_TIMEOUT: return "device wait timed out";
+    case QGEMM_ERR_NO_DEVICE: return "no usable sm_103 device";
+    case QGEMM_ERR_WORKSPACE: return "workspace missing or too small";
+    default: return "unknown status";
+  }
+}
+
+int qgemm_debug_unsatisfied_wait(uint64_t limit_ns, void *stream) {
+  int rc = device_ready();
+  if (rc) return rc;
+  return debug_unsatisfied_wait(limit_ns, static_cast<cudaStream_t>(stream));
+}
+
+int qgemm_probe_peak(int which, double seconds, double *tflops, void *stream) {
+  if (which < 0 || which > 3) return -1;
+  if (!(seconds > 0.0) || seconds > 60.0) return -2;
+  if (tflops == nullptr) return -3;
+  int rc = device_ready();
+  if (rc) return rc;
+  return probe_peak(which, seconds, tflops, static_cast<cudaStream_t>(stream));
+}
+
+const char *qgemm_version(void) { return "gb300-qgemm 0.1"; }
+
+}  // extern "C"

@@ -1,0 +1,64 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "qgemm.h"
+
+namespace qg {
+
+// One operand as the kernels see it: element (r, c) of the STORED matrix,
+// component s, lives at ptr + s*cs + r*rs + c*ld (reals).  Interleaved:
+// cs = 1, rs = 4, ld = 4*ld_q.  Split planes: cs = plane stride, rs = 1.
+struct MatView {
+  const void *ptr;
+  int64_t rows, cols;  // stored extent (quaternions)
+  int64_t ld;          // leading dimension (quaternions)
+  int64_t ps;          // plane stride (reals, split layout only)
+};
+
+// Description of one GEMM after validation.
+struct GemmDesc {
+  int opA, opB;
+  int64_t m, n, k;
+  double alpha[4], beta[4];
+  MatView A, B;
+  void *C;
+  int64_t ldc, psc;
+  int layout;
+  bool beta_zero;
+};
+
+inline bool op_trans(int op) { return op == QGEMM_OP_T || op == QGEMM_OP_H; }
+inline bool op_conj(int op) { return op == QGEMM_OP_C || op == QGEMM_OP_H; }
+
+// Tensor-map encoder from the driver (fetched once, without linking libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled_fn();
+
+// Device wait limit for bounded spins (env QGEMM_WAIT_LIMIT_MS, default 2000).
+uint64_t wait_limit_ns();
+
+// Checks that a usable device is current; returns a QGEMM status.
+int device_ready();
+
+// Launchers (return QGEMM status codes).
+int launch_fp64_gemm(const GemmDesc &d, cudaStream_t stream);
+int launch_scale(const GemmDesc &d, bool fp64, cudaStream_t stream);
+int split_workspace_bytes(const GemmDesc &d, size_t *bytes);
+int launch_split_gemm(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_t stream);
+
+// Device status words of each translation unit (read and cleared).
+int fp64_take_device_error();
+int split_take_device_error();
+int grouped_take_device_error();
+int misc_take_device_error();
+int debug_unsatisfied_wait(uint64_t limit_ns, cudaStream_t stream);
+int probe_peak(int which, double seconds, double *tflops, cudaStream_t stream);
+
+}  // namespace qg

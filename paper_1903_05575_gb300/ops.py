@@ -1,0 +1,115 @@
+"""Thin torch-facing binding over the C ABI (argument marshalling only).
+
+Tensors are column-major quaternion matrices:
+  interleaved: shape (cols, ld, 4), C-contiguous; component s of element
+               (r, c) at [c, r, s] -- four contiguous reals per element (Sec. 4)
+  planes:      shape (4, cols, ld), C-contiguous; plane s at [s] (Sec. 2.2)
+Row counts are given explicitly (rows <= ld).  float64 tensors run the FP64
+path, float32 tensors the split-BF16 path.  Every call goes to the CUDA
+library on torch's current stream; there is no CPU fallback.
+"""
+import torch
+
+from . import _abi
+
+_workspaces = {}
+
+
+def geometry(X, layout):
+    """(ld, plane_stride, stored_cols) of a tensor in the given layout."""
+    if not X.is_contiguous():
+        raise ValueError("quaternion tensors must be contiguous")
+    if layout == "interleaved":
+        if X.dim() != 3 or X.shape[2] != 4:
+            raise ValueError("interleaved tensors have shape (cols, ld, 4)")
+        return X.shape[1], 0, X.shape[0]
+    if X.dim() != 3 or X.shape[0] != 4:
+        raise ValueError("split-plane tensors have shape (4, cols, ld)")
+    return X.shape[2], X.shape[1] * X.shape[2], X.shape[1]
+
+
+def precision_of(dtype):
+    if dtype == torch.float64:
+        return "fp64"
+    if dtype == torch.float32:
+        return "split_bf16"
+    raise TypeError("quaternion GEMM takes float64 (FP64 path) or float32 (split-BF16 path)")
+
+
+def workspace(nbytes, device):
+    """A cached device workspace of at least nbytes (grown on demand)."""
+    if nbytes == 0:
+        return None
+    key = torch.device(device).index or 0
+    ws = _workspaces.get(key)
+    if ws is None or ws.numel() < nbytes:
+        ws = torch.empty(max(nbytes, 1 << 20), dtype=torch.uint8, device=device)
+        _workspaces[key] = ws
+    return ws
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def qgemm(opA, opB, m, n, k, alpha, A, B, beta, C, layout="interleaved", ws=None,
+          stream=None):
+    """C <- alpha op(A) op(B) + beta C on the GPU (C is updated in place)."""
+    prec = precision_of(C.dtype)
+    if A.dtype != C.dtype or B.dtype != C.dtype:
+        raise TypeError("A, B and C must share a dtype")
+    L = _abi.lib()
+    lda, psA, _ = geometry(A, layout)
+    ldb, psB, _ = geometry(B, layout)
+    ldc, psC, _ = geometry(C, layout)
+    need = L.qgemm_workspace_bytes(_abi.OP[opA], _abi.OP[opB], m, n, k, _abi.LAYOUT[layout],
+                                   _abi.PRECISION[prec])
+    if ws is None:
+        ws = workspace(need, C.device)
+    wptr = ws.data_ptr() if ws is not None else None
+    wbytes = ws.numel() * ws.element_size() if ws is not None else 0
+    rc = L.qgemm(_abi.OP[opA], _abi.OP[opB], m, n, k, _abi.q4(alpha), A.data_ptr(), lda, psA,
+                 B.data_ptr(), ldb, psB, _abi.q4(beta), C.data_ptr(), ldc, psC,
+                 _abi.LAYOUT[layout], _abi.PRECISION[prec], wptr, wbytes, _stream_handle(stream))
+    _abi.check(rc, "qgemm")
+    return C
+
+
+def qgemm_backward(X, W, dY, mb, k, n, dX=None, dW=None, accumulate=False,
+                   layout="interleaved", ws=None, stream=None):
+    """dX = dY W^H and dW = X^H dY for Y = X W (either output may be None)."""
+    prec = precision_of(X.dtype)
+    L = _abi.lib()
+    ldx, psx, _ = geometry(X, layout)
+    ldw, psw, _ = geometry(W, layout)
+    lddy, psdy, _ = geometry(dY, layout)
+    lddx, psdx = (geometry(dX, layout)[:2] if dX is not None else (max(mb, 1), 0))
+    lddw, psdw = (geometry(dW, layout)[:2] if dW is not None else (max(k, 1), 0))
+    need = L.qgemm_backward_workspace_bytes(mb, k, n, _abi.LAYOUT[layout], _abi.PRECISION[prec])
+    if ws is None:
+        ws = workspace(need, X.device)
+    wptr = ws.data_ptr() if ws is not None else None
+    wbytes = ws.numel() * ws.element_size() if ws is not None else 0
+    rc = L.qgemm_backward(mb, k, n, X.data_ptr(), ldx, psx, W.data_ptr(), ldw, psw,
+                          dY.data_ptr(), lddy, psdy,
+                          dX.data_ptr() if dX is not None else None, lddx, psdx,
+                          dW.data_ptr() if dW is not None else None, lddw, psdw,
+                          1 if accumulate else 0, _abi.LAYOUT[layout], _abi.PRECISION[prec],
+                          wptr, wbytes, _stream_handle(stream))
+    _abi.check(rc, "qgemm_backward")
+    return dX, dW
+
+
+def last_device_error():
+    return _abi.lib().qgemm_get_last_device_error()
+
+
+def probe_peak(which, seconds=0.3, stream=None):
+    """Measured TFLOP/s of a pipe: 0 DMMA, 1 DFMA, 2 FFMA, 3 tcgen05 BF16."""
+    import ctypes
+    out = ctypes.c_double(0.0)
+    rc = _abi.lib().qgemm_probe_peak(which, seconds, ctypes.byref(out), _stream_handle(stream))
+    _abi.check(rc, "qgemm_probe_peak")
+    return out.value

@@ -1,0 +1,104 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds, loads,
+exports every entry point declared in include/qgemm.h, and rejects invalid
+arguments with LAPACK-style -i codes before touching a device."""
+import os
+import re
+
+import pytest
+
+from paper_1903_05575_gb300 import _abi
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                      "include", "qgemm.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|size_t|const char \*)\s*(qgemm\w*)\s*\(", src,
+                                 flags=re.M)))
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for required in ("qgemm", "qgemm_batched_grouped", "qgemm_backward"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = _abi.lib()
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert missing == []
+    assert set(declared_functions()) <= set(_abi.SIGNATURES)
+
+
+def _call(**kw):
+    a = dict(opA=0, opB=0, m=4, n=4, k=4, alpha=_abi.q4([1, 0, 0, 0]), A=64, lda=4, psA=0,
+             B=64, ldb=4, psB=0, beta=_abi.q4([0, 0, 0, 0]), C=64, ldc=4, psC=0, layout=0,
+             precision=0, ws=None, wsb=0, stream=None)
+    a.update(kw)
+    return _abi.lib().qgemm(a["opA"], a["opB"], a["m"], a["n"], a["k"], a["alpha"], a["A"],
+                            a["lda"], a["psA"], a["B"], a["ldb"], a["psB"], a["beta"], a["C"],
+                            a["ldc"], a["psC"], a["layout"], a["precision"], a["ws"], a["wsb"],
+                            a["stream"])
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(opA=4), -1), (dict(opB=-1), -2), (dict(m=-1), -3), (dict(n=-2), -4), (dict(k=-1), -5),
+    (dict(alpha=None), -6), (dict(A=None), -7), (dict(lda=3), -8), (dict(B=None), -10),
+    (dict(ldb=0), -11), (dict(beta=None), -13), (dict(C=None), -14), (dict(ldc=2), -15),
+    (dict(layout=2), -17), (dict(precision=7), -18),
+    (dict(layout=1, psA=15, psB=16, psC=16), -9), (dict(layout=1, psA=16, psB=3, psC=16), -12),
+    (dict(layout=1, psA=16, psB=16, psC=0), -16),
+    (dict(A=68), -7),              # FP64 element misaligned
+    (dict(opA=1, m=6, lda=4, ldc=6), 0),  # op T: stored A is k x m, lda >= k = 4 is fine ...
+    (dict(opA=0, m=6, lda=4, ldc=6), -8),  # ... op N: lda >= m = 6 is not
+])
+def test_argument_checks(kw, code):
+    rc = _call(**kw)
+    if code == 0:
+        assert rc in (0, _abi.ERR_NO_DEVICE)
+    else:
+        assert rc == code
+
+
+def test_quick_returns_need_no_device():
+    assert _call(m=0, A=None, B=None, C=None) == 0
+    assert _call(n=0, A=None, B=None, C=None) == 0
+
+
+def test_alpha_zero_does_not_reference_operands():
+    # alpha == 0: A and B are not read, so NULL is accepted (C <- beta C)
+    rc = _call(alpha=_abi.q4([0, 0, 0, 0]), A=None, B=None)
+    assert rc in (0, _abi.ERR_NO_DEVICE)
+
+
+def test_split_precision_needs_workspace():
+    L = _abi.lib()
+    need = L.qgemm_workspace_bytes(0, 0, 64, 64, 64, 0, 1)
+    if need == 0:
+        pytest.skip("split path needs no workspace")
+    assert _call(precision=1, m=64, n=64, k=64, lda=64, ldb=64, ldc=64) == -19
+    assert _call(precision=1, m=64, n=64, k=64, lda=64, ldb=64, ldc=64, ws=256,
+                 wsb=need - 1) == -20
+
+
+def test_backward_argument_numbers():
+    L = _abi.lib()
+    rc = L.qgemm_backward(-1, 4, 4, 64, 4, 0, 64, 4, 0, 64, 4, 0, 64, 4, 0, 64, 4, 0, 0, 0, 0,
+                          None, 0, None)
+    assert rc == -1
+    # dX = dY W^H with a bad ldw (W is k x n, ldw >= k): argument 8
+    rc = L.qgemm_backward(4, 6, 5, 64, 4, 0, 64, 5, 0, 64, 4, 0, 64, 4, 0, None, 6, 0, 0, 0, 0,
+                          None, 0, None)
+    assert rc == -8
+    # dW = X^H dY with dW's ld too small (dW is k x n, lddw >= k = 6): argument 17
+    rc = L.qgemm_backward(4, 6, 5, 64, 4, 0, 64, 6, 0, 64, 4, 0, None, 4, 0, 64, 5, 0, 0, 0, 0,
+                          None, 0, None)
+    assert rc == -17
+
+
+def test_status_strings():
+    L = _abi.lib()
+    for rc in (0, 1, 2, 3, 4, 5, -3):
+        assert len(L.qgemm_status_string(rc)) > 0
