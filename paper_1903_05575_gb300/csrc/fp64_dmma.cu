@@ -30,6 +30,7 @@ constexpr int kBNQ = 32;      // quaternion columns of C per CTA
 constexpr int kBKQ = 16;      // quaternion k per pipeline stage
 constexpr int kStages = 3;
 constexpr int kThreads = 128; // 4 warps, warp w owns rows [8w, 8w+8) x all 32 columns
+constexpr int kGroupM = 16;   // row-tiles per rasterisation group
 constexpr int kTileElems = kBMQ * kBKQ * 4;  // = kBKQ * kBNQ * 4 (doubles)
 constexpr uint32_t kTileBytes = kTileElems * sizeof(double);
 static_assert(kBMQ * kBKQ == kBKQ * kBNQ, "A and B tiles have the same size");
@@ -115,8 +116,15 @@ __global__ void __launch_bounds__(kThreads)
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
-  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * kBMQ;
-  const int64_t n0 = static_cast<int64_t>(blockIdx.y) * kBNQ;
+  // grouped rasterisation: runs of kGroupM row-tiles share their B column
+  // panels in L2 while they sweep the columns
+  const int64_t tiles_m = (p.m + kBMQ - 1) / kBMQ, tiles_n = (p.n + kBNQ - 1) / kBNQ;
+  const int64_t tid_lin = static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x;
+  const int64_t per_group = kGroupM * tiles_n;
+  const int64_t first_m = (tid_lin / per_group) * kGroupM;
+  const int64_t gsize = min(tiles_m - first_m, static_cast<int64_t>(kGroupM));
+  const int64_t i0 = (first_m + (tid_lin % per_group) % gsize) * kBMQ;
+  const int64_t n0 = ((tid_lin % per_group) / gsize) * kBNQ;
   const int ktiles = static_cast<int>((p.k + kBKQ - 1) / kBKQ);
   const bool any_tma = p.tmaA || p.tmaB;
   const uint32_t tx_bytes = (p.tmaA ? kTileBytes : 0u) + (p.tmaB ? kTileBytes : 0u);

@@ -1,0 +1,121 @@
+"""Split-BF16 path (tcgen05) against the FP64 oracle, through the C ABI.
+
+Inputs are float32; the oracle computes in FP64 on the same float32 values.
+Bar: relative Frobenius error <= 2e-6 for N(0,1) and for the wide-range
+(2^(u_r + v_c)) inputs; small integers (exactly representable, partial sums
+below 2^24) bit-exact; padding rows untouched."""
+import numpy as np
+import pytest
+import torch
+
+import qsynth
+from oracle import oracle as orc
+from paper_1903_05575_gb300 import _abi, ops
+from tests.gpu_util import gpu_run, make_case, oracle_full, padding, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+OPS = ("N", "T", "C", "H")
+TOL = 2e-6
+ALPHA = np.array([0.5, -1.0, 2.0, 0.25])
+BETA = np.array([-1.0, 0.5, 0.0, 1.5])
+
+
+def check(opA, opB, m, n, k, layout, seed, kind="normal", alpha=ALPHA, beta=BETA, tol=TOL):
+    A, B, C = make_case(opA, opB, m, n, k, layout, seed, kind, dtype=np.float32)
+    ref = oracle_full(opA, opB, m, n, k, alpha, A, B, beta, C, layout)
+    got = gpu_run(opA, opB, m, n, k, alpha, A, B, beta, C, layout, dtype=torch.float32)
+    g, r = qsynth.components(got, m, layout), qsynth.components(ref, m, layout)
+    if kind == "int":
+        bad = np.argwhere(g != r)
+        assert bad.size == 0, "not bit-exact at %d entries, first %s: got %s want %s" % (
+            len(bad), bad[:4].tolist(), g[tuple(bad[0])], r[tuple(bad[0])])
+        err = 0.0
+    else:
+        err = rel_fro(g, r)
+        assert err <= tol, "relative Frobenius error %.3e" % err
+    assert np.all(np.isnan(padding(got, m, layout))), "padding rows written"
+    return err
+
+
+def test_small_int_exact_one_tile():
+    check("N", "N", 128, 64, 8, "interleaved", 1, kind="int",
+          alpha=np.array([1.0, 0, 0, 0]), beta=np.zeros(4))
+
+
+def test_normal_one_tile():
+    check("N", "N", 128, 64, 40, "interleaved", 2)
+
+
+@pytest.mark.parametrize("layout", qsynth.LAYOUTS)
+@pytest.mark.parametrize("opA", OPS)
+@pytest.mark.parametrize("opB", OPS)
+def test_op_pairs_ragged(opA, opB, layout):
+    check(opA, opB, 150, 70, 45, layout, seed=31 + 4 * OPS.index(opA) + OPS.index(opB))
+
+
+@pytest.mark.parametrize("layout", qsynth.LAYOUTS)
+@pytest.mark.parametrize("opA,opB", [("N", "N"), ("T", "H"), ("C", "T"), ("H", "C")])
+def test_small_int_exact(opA, opB, layout):
+    check(opA, opB, 200, 90, 77, layout, seed=400 + OPS.index(opA), kind="int",
+          alpha=np.array([1.0, -2.0, 0.0, 1.0]), beta=np.array([2.0, 0, 1.0, -1.0]))
+
+
+@pytest.mark.parametrize("mnk", [(1, 1, 1), (7, 9, 8), (129, 65, 9), (1, 100, 300), (257, 3, 17)])
+def test_edge_sizes(mnk):
+    m, n, k = mnk
+    for layout in qsynth.LAYOUTS:
+        check("N", "H", m, n, k, layout, seed=m + 7 * n + 13 * k)
+
+
+def test_beta_zero_does_not_read_c():
+    m, n, k = 130, 66, 30
+    A, B, C = make_case("N", "N", m, n, k, "interleaved", 5, dtype=np.float32)
+    C[:] = np.nan
+    got = gpu_run("N", "N", m, n, k, ALPHA, A, B, np.zeros(4), C, "interleaved",
+                  dtype=torch.float32)
+    assert not np.any(np.isnan(qsynth.components(got, m, "interleaved")))
+
+
+def test_wide_range_inputs():
+    """Components N(0,1) * 2^(u_r + v_c), u, v in [-20, 20] per row and column."""
+    err = check("N", "N", 256, 128, 256, "interleaved", 8, kind="scaled")
+    print("wide-range rel err %.3e" % err)
+
+
+def test_workspace_checks():
+    L = _abi.lib()
+    m = n = k = 64
+    need = L.qgemm_workspace_bytes(0, 0, m, n, k, 0, 1)
+    assert need > 0
+    A = torch.zeros((k, m, 4), dtype=torch.float32, device="cuda")
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    rc = L.qgemm(0, 0, m, n, k, _abi.q4([1, 0, 0, 0]), A.data_ptr(), m, 0, A.data_ptr(), k, 0,
+                 _abi.q4([0, 0, 0, 0]), A.data_ptr(), m, 0, 0, 1, ws.data_ptr(), need - 1, None)
+    assert rc == -20
+
+
+def _sampled(n, kind, seed, layout="interleaved", opA="N", opB="N"):
+    m = k = n
+    alpha, beta = qsynth.unit_quaternion(seed), qsynth.unit_quaternion(seed + 1)
+    A, B, C = make_case(opA, opB, m, n, k, layout, seed, kind, pad=(0, 0, 0), dtype=np.float32)
+    got = gpu_run(opA, opB, m, n, k, alpha, A, B, beta, C, layout, dtype=torch.float32)
+    g = qsynth.rng(seed + 3)
+    rows = np.concatenate([np.repeat(g.integers(0, m, 2), n), g.integers(0, m, 2048)])
+    cols = np.concatenate([np.tile(np.arange(n), 2), g.integers(0, n, 2048)])
+    ref = orc.qgemm_entries(opA, opB, m, n, k, alpha, A, B, beta, C, rows, cols, layout=layout)
+    return rel_fro(qsynth.components(got, m, layout)[rows, cols], ref)
+
+
+@pytest.mark.parametrize("kind", ["normal", "scaled"])
+def test_sampled_2048(kind):
+    err = _sampled(2048, kind, 2100)
+    print("2048 %s sampled rel err %.3e" % (kind, err))
+    assert err <= TOL
+
+
+@pytest.mark.parametrize("kind", ["normal", "scaled"])
+def test_sampled_8192(kind):
+    err = _sampled(8192, kind, 8200)
+    print("8192 %s sampled rel err %.3e" % (kind, err))
+    assert err <= TOL
