@@ -40,6 +40,8 @@ def parse():
     p.add_argument("--layout", default="interleaved", choices=["interleaved", "planes"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-split", action="store_true")
+    p.add_argument("--split-size", type=int, default=8192)
     return p.parse_args()
 
 
@@ -197,6 +199,81 @@ def max_over_ranks(world, x):
     return float(t.item())
 
 
+# ----------------------------------------------------- split section ---
+def split_section(n, fp64_tflops, steps=5):
+    """The split-BF16 path on m = n = k = n, FP32 components iid N(0,1),
+    op N,N, interleaved, unit-quaternion alpha and beta: effective and issued
+    TFLOP/s, sampled error against the FP64 oracle, speedup over the FP64
+    path's measured rate."""
+    import json as _json
+    import numpy as np
+    import torch
+
+    import qsynth
+    from paper_1903_05575_gb300 import _abi, ops
+    dev = torch.device("cuda", torch.cuda.current_device())
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2203)
+    shape = (n, n, 4)
+    A = torch.randn(shape, dtype=torch.float32, device=dev, generator=gen)
+    B = torch.randn(shape, dtype=torch.float32, device=dev, generator=gen)
+    C0 = torch.randn(shape, dtype=torch.float32, device=dev, generator=gen)
+    C = C0.clone()
+    alpha, beta = qsynth.unit_quaternion(2204), qsynth.unit_quaternion(2205)
+    L = _abi.lib()
+    need = L.qgemm_workspace_bytes(0, 0, n, n, n, 0, 1)
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    al, be = _abi.q4(alpha), _abi.q4(beta)
+    stream = torch.cuda.current_stream()
+
+    def step(Cout):
+        rc = L.qgemm(0, 0, n, n, n, al, A.data_ptr(), n, 0, B.data_ptr(), n, 0, be,
+                     Cout.data_ptr(), n, 0, 0, 1, ws.data_ptr(), need, stream.cuda_stream)
+        if rc != 0:
+            raise _abi.QgemmError(rc)
+
+    for _ in range(2):
+        step(C)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step(C)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    eff = 32.0 * n ** 3 / (ms * 1e-3) / 1e12
+    # error of one result on sampled entries against the FP64 oracle
+    C.copy_(C0)
+    step(C)
+    torch.cuda.synchronize()
+    from oracle import oracle as orc
+    g = np.random.default_rng(9)
+    rows, cols = g.integers(0, n, 512), g.integers(0, n, 512)
+    Ah, Bh, Ch = (X.double().cpu().numpy() for X in (A, B, C0))
+    ref = orc.qgemm_entries("N", "N", n, n, n, alpha, Ah, Bh, beta, Ch, rows, cols)
+    got = qsynth.components(C.double().cpu().numpy(), n, "interleaved")[rows, cols]
+    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    peaks = {}
+    try:
+        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    return {"config": "split-bf16 qgemm m=n=k=%d op=NN interleaved fp32 N(0,1), 3-term split, "
+                      "6 term products" % n,
+            "value": eff, "unit": "TFLOP/s", "ms_per_call": ms,
+            "issued_bf16_tflops": 6.0 * eff,
+            "frac_of_bf16_peak_issued": 6.0 * eff / bf16_peak,
+            "frac_of_bf16_peak_effective": eff / bf16_peak,
+            "bf16_peak": bf16_peak,
+            "bf16_peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)"
+                                if "bf16_tflops" in peaks else "fallback 1900",
+            "rel_err_sampled": err, "tolerance": 2e-6,
+            "speedup_vs_fp64_path": eff / fp64_tflops,
+            "kernels_per_call": 3, "workspace_bytes": need}
+
+
 # -------------------------------------------------------------- impls ---
 def run_reference(args):
     """The oracle as the reference arm: each step is a bounded sample of the
@@ -351,6 +428,10 @@ def run_ours(args):
         G = qs.components(got, m, layout)[rows, cols]
         err = float(np.linalg.norm(G - ref) / np.linalg.norm(ref))
 
+    split = None
+    if not args.no_split:
+        split = split_section(args.split_size, achieved)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_baseline(n, layout=layout)
@@ -373,6 +454,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": args.steps,
         "cpu_baseline": cpu,
+        "split_bf16": split,
     }
     print(json.dumps(line), flush=True)
 
