@@ -120,6 +120,37 @@ size_t qgemm_workspace_bytes(int opA, int opB, int64_t m, int64_t n, int64_t k,
                              int layout, int precision);
 
 /*
+ * qgemm_split_noalloc: the split-BF16 qgemm() for callers that cannot
+ * allocate device memory -- for example code that runs while a CUDA graph is
+ * being captured (cudaMalloc is not allowed then), code whose device memory
+ * is all owned by another allocator, or a plain C caller with no allocator of
+ * its own.  It takes no workspace: the split operands go to a scratch array
+ * of QGEMM_NOALLOC_SCRATCH_BYTES that the library keeps in device memory
+ * (every device that loads the library holds it until the process exits).
+ * The paper has no counterpart; it is an interface convenience.
+ *
+ * Arguments 1-17 and 18 (stream) as in qgemm() with precision
+ * QGEMM_FP32_SPLIT_BF16 (float data).  Returns QGEMM_ERR_WORKSPACE, before
+ * launching anything, when the problem needs more than
+ * QGEMM_NOALLOC_SCRATCH_BYTES (qgemm_workspace_bytes() gives the need; for
+ * square problems the largest that fits is m = n = k = 744).
+ * It calls no allocator.  The first call on a device looks up the scratch
+ * array's device address, so make it once before any stream capture.  All
+ * calls share the one array: calls that can overlap on the GPU (different
+ * streams without ordering between them) race and give wrong results.  Each
+ * call rewrites every scratch byte its kernels read, so nothing has to be
+ * cleared between calls.
+ */
+#define QGEMM_NOALLOC_SCRATCH_BYTES (64u << 20)
+int qgemm_split_noalloc(int opA, int opB, int64_t m, int64_t n, int64_t k,
+                        const double alpha[4],
+                        const void *A, int64_t lda, int64_t psA,
+                        const void *B, int64_t ldb, int64_t psB,
+                        const double beta[4],
+                        void *C, int64_t ldc, int64_t psC,
+                        int layout, void *stream);
+
+/*
  * One problem of a grouped batch (host struct).  Same meaning as the qgemm()
  * arguments of the same names; ops are QGEMM_OP_* values.
  */

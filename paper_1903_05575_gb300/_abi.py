@@ -19,6 +19,7 @@ ERR_CUDA = 2
 ERR_TIMEOUT = 3
 ERR_NO_DEVICE = 4
 ERR_WORKSPACE = 5
+NOALLOC_SCRATCH_BYTES = 64 << 20
 
 i32, i64, sz, vp, dp = (ctypes.c_int, ctypes.c_int64, ctypes.c_size_t, ctypes.c_void_p,
                         ctypes.POINTER(ctypes.c_double))
@@ -39,6 +40,8 @@ SIGNATURES = {
     "qgemm": (i32, [i32, i32, i64, i64, i64, dp, vp, i64, i64, vp, i64, i64, dp, vp, i64, i64,
                     i32, i32, vp, sz, vp]),
     "qgemm_workspace_bytes": (sz, [i32, i32, i64, i64, i64, i32, i32]),
+    "qgemm_split_noalloc": (i32, [i32, i32, i64, i64, i64, dp, vp, i64, i64, vp, i64, i64, dp,
+                                  vp, i64, i64, i32, vp]),
     "qgemm_batched_grouped": (i32, [ctypes.POINTER(QgemmProblem), i64, i32, i32, vp, sz, vp]),
     "qgemm_grouped_workspace_bytes": (sz, [ctypes.POINTER(QgemmProblem), i64, i32, i32]),
     "qgemm_grouped_prepare": (i32, [ctypes.POINTER(QgemmProblem), i64, i32, i32, vp, sz, vp]),

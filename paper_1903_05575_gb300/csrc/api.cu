@@ -149,6 +149,31 @@ int qgemm(int opA, int opB, int64_t m, int64_t n, int64_t k, const double alpha[
   return launch_split_gemm(d, workspace, workspace_bytes, s);
 }
 
+int qgemm_split_noalloc(int opA, int opB, int64_t m, int64_t n, int64_t k,
+                        const double alpha[4], const void *A, int64_t lda, int64_t psA,
+                        const void *B, int64_t ldb, int64_t psB, const double beta[4], void *C,
+                        int64_t ldc, int64_t psC, int layout, void *stream) {
+  GemmDesc d;
+  int rc = validate_gemm(opA, opB, m, n, k, alpha, A, lda, psA, B, ldb, psB, beta, C, ldc, psC,
+                         layout, QGEMM_FP32_SPLIT_BF16, &d);
+  if (rc) return rc;
+  size_t need = 0;
+  if (d.k > 0) {
+    rc = split_workspace_bytes(d, &need);
+    if (rc) return rc;
+  }
+  if (need > static_cast<size_t>(QGEMM_NOALLOC_SCRATCH_BYTES)) return QGEMM_ERR_WORKSPACE;
+  if (m == 0 || n == 0) return QGEMM_SUCCESS;
+  rc = device_ready();
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (d.k == 0) return launch_scale(d, false, s);
+  void *scratch = nullptr;
+  rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  return launch_split_gemm(d, scratch, static_cast<size_t>(QGEMM_NOALLOC_SCRATCH_BYTES), s);
+}
+
 size_t qgemm_workspace_bytes(int opA, int opB, int64_t m, int64_t n, int64_t k, int layout,
                              int precision) {
   if (precision != QGEMM_FP32_SPLIT_BF16) return 0;

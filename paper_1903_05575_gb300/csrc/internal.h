@@ -52,6 +52,11 @@ int launch_fp64_gemm(const GemmDesc &d, cudaStream_t stream);
 int launch_scale(const GemmDesc &d, bool fp64, cudaStream_t stream);
 int split_workspace_bytes(const GemmDesc &d, size_t *bytes);
 int launch_split_gemm(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_t stream);
+int noalloc_scratch(void **out);
+int validate_gemm(int opA, int opB, int64_t m, int64_t n, int64_t k, const double *alpha,
+                  const void *A, int64_t lda, int64_t psA, const void *B, int64_t ldb,
+                  int64_t psB, const double *beta, void *C, int64_t ldc, int64_t psC,
+                  int layout, int precision, GemmDesc *d);
 
 // Device status words of each translation unit (read and cleared).
 int fp64_take_device_error();

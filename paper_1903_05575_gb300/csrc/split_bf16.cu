@@ -35,6 +35,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -702,6 +703,39 @@ int probe_tcgen05_bf16(double seconds, double *tflops, cudaStream_t stream) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return rc;
+}
+
+// ------------------------------------------------ fixed-scratch variant ---
+// Scratch for qgemm_split_noalloc(): the split operands live in this array
+// instead of a caller workspace.  Every device that loads this module holds
+// it until the process exits.  Host code must not use the symbol's host-side
+// stand-in as a device address; the address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[QGEMM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64];
+}  // namespace
+
+// Device address of the scratch on the current device, looked up once per
+// device (the first call on a device does this; make it before any capture).
+int noalloc_scratch(void **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return QGEMM_ERR_NO_DEVICE;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) {
+      cudaGetLastError();
+      return QGEMM_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return QGEMM_SUCCESS;
 }
 
 int split_take_device_error() {
