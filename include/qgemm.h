@@ -150,6 +150,7 @@ int qgemm_split_noalloc(int opA, int opB, int64_t m, int64_t n, int64_t k,
                         void *C, int64_t ldc, int64_t psC,
                         int layout, void *stream);
 
+
 /*
  * One problem of a grouped batch (host struct).  Same meaning as the qgemm()
  * arguments of the same names; ops are QGEMM_OP_* values.
@@ -164,33 +165,76 @@ typedef struct qgemm_problem {
 } qgemm_problem;
 
 /*
- * qgemm_batched_grouped: `count` independent problems in one persistent
- * launch.  `problems` is a HOST array; it is validated, turned into a device
- * tile schedule inside `workspace` (copied with cudaMemcpyAsync on `stream`),
- * and the grouped kernel is launched.  Returns -(1000*p + i) when argument i
- * of problem p is invalid (i numbered as in qgemm()), -1/-2 for problems /
- * count, and -(3..7) for the trailing arguments.
+ * Plan of a grouped batch, filled by qgemm_grouped_prepare() (host struct,
+ * owned by the caller; it only describes what the prepare call wrote into
+ * the workspace, so it can be copied freely).
+ */
+typedef struct qgemm_grouped_plan {
+    void *workspace;          /* device schedule written by prepare           */
+    size_t workspace_bytes;   /* bytes of it in use                           */
+    int32_t layout, precision;
+    int64_t count;            /* problems                                     */
+    int64_t tiles;            /* output tiles in the schedule                 */
+    int32_t grid;             /* persistent CTAs launched                     */
+    int32_t reserved0;
+    int64_t desc_offset;      /* byte offsets of the schedule's sections      */
+    int64_t tile_offset;
+    int64_t data_offset;
+    int64_t reserved[4];
+} qgemm_grouped_plan;
+
+/*
+ * qgemm_batched_grouped: `count` independent problems C_p <- alpha_p op(A_p)
+ * op(B_p) + beta_p C_p (each as in qgemm()) in one persistent launch: the
+ * batching of many uneven products; the tile shape of each problem comes
+ * from a per-size-bucket table (qgemm_grouped_set_tile_table), the GPU
+ * analogue of the paper's per-machine choice of blocking parameters
+ * (Sec. 3.2, Sec. 5).  `problems` is a HOST array.  Equivalent to
+ * qgemm_grouped_prepare() followed by qgemm_grouped_launch().
+ * Return codes: -1 problems, -2 count, -3 layout, -4 precision, -5 workspace,
+ * -6 workspace_bytes, -8 plan; -(1000*(p+1) + i) when argument i (numbered as
+ * in qgemm()) of problem p is invalid; positive QGEMM_ERR_* otherwise.
  */
 int qgemm_batched_grouped(const qgemm_problem *problems, int64_t count,
                           int layout, int precision,
                           void *workspace, size_t workspace_bytes,
                           void *stream);
 
-/* Workspace for qgemm_batched_grouped() with these problems. */
+/* Workspace for a grouped batch with these problems (0 if they are invalid). */
 size_t qgemm_grouped_workspace_bytes(const qgemm_problem *problems, int64_t count,
                                      int layout, int precision);
 
 /*
- * Split form for CUDA-graph capture: qgemm_grouped_prepare() validates the
- * problems and writes the schedule into `workspace` (asynchronous copy on
- * `stream`); qgemm_grouped_launch() only launches the persistent kernel(s)
- * that read it, so it can be captured and replayed.  The workspace must not
- * be modified between the two.
+ * Split form for CUDA-graph capture.  qgemm_grouped_prepare() validates the
+ * problems, encodes their tensor maps and tile schedule on the host and
+ * copies them into `workspace` with cudaMemcpyAsync on `stream` (from
+ * pageable host memory: do not call it during stream capture); it fills
+ * *plan.  qgemm_grouped_launch() only resets the schedule's tile counter
+ * (cudaMemsetAsync) and launches the persistent kernel, so it can be captured
+ * and replayed.  Matrix pointers, sizes and scalars are frozen at prepare
+ * time; the matrices' contents are read at launch time.  The workspace must
+ * not be modified between the two, and launches sharing one workspace must
+ * not overlap on the GPU.
  */
 int qgemm_grouped_prepare(const qgemm_problem *problems, int64_t count,
                           int layout, int precision,
-                          void *workspace, size_t workspace_bytes, void *stream);
-int qgemm_grouped_launch(void *workspace, void *stream);
+                          void *workspace, size_t workspace_bytes, void *stream,
+                          qgemm_grouped_plan *plan);
+int qgemm_grouped_launch(const qgemm_grouped_plan *plan, void *stream);
+
+/*
+ * Tile-shape table of the grouped path (the autotuner's output).  Problems
+ * fall into 25 buckets, index 5*rm + rn, where rm (rn) is the range of m (n)
+ * among (<=16, <=32, <=64, <=128, >128).  table[b] is a shape index (see
+ * qgemm_grouped_tile_info).  table == NULL restores the built-in choice
+ * (per dimension the shape with least padding).  FP64 only.
+ */
+int qgemm_grouped_set_tile_table(int precision, const int32_t *table, int32_t entries);
+
+/* Shapes and buckets of the grouped path: number of shapes, their quaternion
+ * rows / columns (arrays of at least 8), number of buckets, the 4 range edges. */
+int qgemm_grouped_tile_info(int32_t *num_shapes, int32_t *shape_m, int32_t *shape_n,
+                            int32_t *num_buckets, int32_t *edges);
 
 /*
  * qgemm_backward: gradients of a quaternion linear map Y = X W, with

@@ -35,6 +35,15 @@ class QgemmProblem(ctypes.Structure):
                 ("C", vp), ("ldc", i64), ("psC", i64)]
 
 
+class QgemmGroupedPlan(ctypes.Structure):
+    """Mirror of struct qgemm_grouped_plan."""
+    _fields_ = [("workspace", vp), ("workspace_bytes", sz), ("layout", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("count", i64), ("tiles", i64),
+                ("grid", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("desc_offset", i64), ("tile_offset", i64), ("data_offset", i64),
+                ("reserved", i64 * 4)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "qgemm": (i32, [i32, i32, i64, i64, i64, dp, vp, i64, i64, vp, i64, i64, dp, vp, i64, i64,
@@ -44,8 +53,11 @@ SIGNATURES = {
                                   vp, i64, i64, i32, vp]),
     "qgemm_batched_grouped": (i32, [ctypes.POINTER(QgemmProblem), i64, i32, i32, vp, sz, vp]),
     "qgemm_grouped_workspace_bytes": (sz, [ctypes.POINTER(QgemmProblem), i64, i32, i32]),
-    "qgemm_grouped_prepare": (i32, [ctypes.POINTER(QgemmProblem), i64, i32, i32, vp, sz, vp]),
-    "qgemm_grouped_launch": (i32, [vp, vp]),
+    "qgemm_grouped_prepare": (i32, [ctypes.POINTER(QgemmProblem), i64, i32, i32, vp, sz, vp,
+                                    ctypes.POINTER(QgemmGroupedPlan)]),
+    "qgemm_grouped_launch": (i32, [ctypes.POINTER(QgemmGroupedPlan), vp]),
+    "qgemm_grouped_set_tile_table": (i32, [i32, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
+    "qgemm_grouped_tile_info": (i32, [ctypes.POINTER(ctypes.c_int32)] * 5),
     "qgemm_backward": (i32, [i64, i64, i64, vp, i64, i64, vp, i64, i64, vp, i64, i64,
                              vp, i64, i64, vp, i64, i64, i32, i32, i32, vp, sz, vp]),
     "qgemm_backward_workspace_bytes": (sz, [i64, i64, i64, i32, i32]),

@@ -1,0 +1,236 @@
+// One output tile of the FP64 quaternion GEMM on DMMA tensor cores, shared by
+// the single-problem kernel and the persistent grouped kernel.
+//
+// Real form: (a b)^c = sum_j L(a)[c][j] b^j with L(a)[c][j] =
+// sign(c xor j, j) a^(c xor j) (Sec. 2.1, Eq. quaternion_prod), so the tile
+// is C_r = L(op(A)) B_r over the real K = 4k.  An m16n8k4 DMMA covers 4
+// quaternion rows (16 real rows: row 4i + c), 8 quaternion columns and one
+// quaternion k element (4 real k: column j); its A fragment is gathered from
+// the staged op(A) tile with the sign of L(a) applied as an integer XOR.
+//
+// The CTA has 4 warps arranged WARPS_M x WARPS_N over a BMQ x BNQ tile; each
+// warp owns 8 quaternion rows and BNQ / WARPS_N columns.  Tiles of 16
+// quaternion k pass through a STAGES-deep shared-memory ring filled by TMA
+// (3-D boxes: component x row x column for interleaved data, row x column x
+// plane for split planes; zero fill past the edges) or by plain loads when a
+// base or stride is not 16-byte aligned.  Ring slots and barrier phases are
+// counted by a running k-block index so a persistent CTA can continue across
+// tiles.
+#pragma once
+#include "common.cuh"
+
+namespace qg {
+namespace fp64 {
+
+constexpr int kBKQ = 16;
+constexpr int kStages = 3;
+constexpr int kThreads = 128;
+constexpr int kMaxTileElems = 32 * kBKQ * 4;  // largest A or B tile (doubles)
+constexpr uint32_t kMaxTileBytes = kMaxTileElems * sizeof(double);
+constexpr size_t kSmemBytes = 2 * kStages * kMaxTileBytes + kStages * sizeof(uint64_t) + 16;
+
+// Operands of one problem as the tile code reads them.
+struct Operands {
+  const double *A;
+  int64_t a_rows, a_cols, lda, psA;
+  const double *B;
+  int64_t b_rows, b_cols, ldb, psB;
+  double *C;
+  int64_t ldc, psC;
+  int64_t m, n, k;
+  double alpha[4], beta[4];
+  uint32_t negmask;
+  int tmaA, tmaB, beta_zero;
+};
+
+// Shared-memory index of component s of stored element (r, c) of a tile with
+// R stored rows and CC stored columns (the TMA box order).
+template <int LAYOUT, int R, int CC>
+__device__ __forceinline__ int tile_idx(int r, int c, int s) {
+  if (LAYOUT == QGEMM_INTERLEAVED) return s + 4 * (r + R * c);
+  return r + R * (c + CC * s);
+}
+
+template <int LAYOUT, int R, int CC>
+__device__ void load_tile_plain(double *dst, const double *base, int64_t rows, int64_t cols,
+                                int64_t ld, int64_t ps, int64_t r0, int64_t c0) {
+  constexpr int N = R * CC * 4;
+  for (int e = threadIdx.x; e < N; e += kThreads) {
+    int r, c, s;
+    if (LAYOUT == QGEMM_INTERLEAVED) {
+      s = e & 3;
+      const int rest = e >> 2;
+      r = rest % R;
+      c = rest / R;
+    } else {
+      r = e % R;
+      c = (e / R) % CC;
+      s = e / (R * CC);
+    }
+    const int64_t gr = r0 + r, gc = c0 + c;
+    double v = 0.0;
+    if (gr < rows && gc < cols)
+      v = LAYOUT == QGEMM_INTERLEAVED ? base[4 * (gr + gc * ld) + s] : base[s * ps + gr + gc * ld];
+    dst[e] = v;
+  }
+}
+
+__device__ __forceinline__ void dmma_16x8x4(double (&d)[4], double a0, double a1, double b0) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k4.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, {%4,%5}, {%6}, "
+      "{%0,%1,%2,%3};\n"
+      : "+d"(d[0]), "+d"(d[1]), "+d"(d[2]), "+d"(d[3])
+      : "d"(a0), "d"(a1), "d"(b0));
+}
+
+__device__ __forceinline__ void tma_box(double *dst, const CUtensorMap *map, uint64_t *bar,
+                                        int layout, int64_t r0, int64_t c0) {
+  if (layout == QGEMM_INTERLEAVED)
+    tma_load_3d(dst, map, bar, 0, static_cast<int>(r0), static_cast<int>(c0));
+  else
+    tma_load_3d(dst, map, bar, static_cast<int>(r0), static_cast<int>(c0), 0);
+}
+
+// Computes and stores one BMQ x BNQ tile at quaternion offset (i0, n0).
+// kb_run counts k-blocks consumed by this CTA so far (ring slot and barrier
+// phase).  Returns false if a bounded wait gave up (after draining its own
+// copies); the caller then stops.
+template <int LAYOUT, bool TA, bool TB, int BMQ, int BNQ>
+__device__ bool tile(const Operands &p, const CUtensorMap *tmA, const CUtensorMap *tmB,
+                     double *sA, double *sB, uint64_t *full, uint32_t &kb_run, int64_t i0,
+                     int64_t n0, uint64_t limit_ns, int *err_word) {
+  constexpr int WARPS_M = BMQ / 8;
+  constexpr int WARPS_N = 4 / WARPS_M;
+  constexpr int WN = BNQ / WARPS_N;  // quaternion columns per warp
+  constexpr int NC = WN / 8;         // m16n8k4 column blocks per warp
+  static_assert(WARPS_M * WARPS_N == 4 && NC >= 1 && WN % 8 == 0, "tile shape");
+  constexpr int A_R = TA ? kBKQ : BMQ, A_C = TA ? BMQ : kBKQ;
+  constexpr int B_R = TB ? BNQ : kBKQ, B_C = TB ? kBKQ : BNQ;
+  constexpr uint32_t kABytes = BMQ * kBKQ * 4 * sizeof(double);
+  constexpr uint32_t kBBytes = BNQ * kBKQ * 4 * sizeof(double);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int wm = warp % WARPS_M, wn = warp / WARPS_M;
+  const int ktiles = static_cast<int>((p.k + kBKQ - 1) / kBKQ);
+  const bool any_tma = p.tmaA || p.tmaB;
+  const uint32_t tx_bytes = (p.tmaA ? kABytes : 0u) + (p.tmaB ? kBBytes : 0u);
+
+  auto issue = [&](int kt) {
+    const uint32_t q = kb_run + kt;
+    const int st = q % kStages;
+    mbar_arrive_expect_tx(&full[st], tx_bytes);
+    const int64_t kk0 = static_cast<int64_t>(kt) * kBKQ;
+    if (p.tmaA) tma_box(sA + st * kMaxTileElems, tmA, &full[st], LAYOUT, TA ? kk0 : i0, TA ? i0 : kk0);
+    if (p.tmaB) tma_box(sB + st * kMaxTileElems, tmB, &full[st], LAYOUT, TB ? n0 : kk0, TB ? kk0 : n0);
+  };
+  if (tid == 0 && any_tma)
+    for (int s = 0; s < kStages && s < ktiles; ++s) issue(s);
+
+  const int c_lane = g & 3;
+  const int compA = c_lane ^ t;
+  const uint32_t negA = ((p.negmask >> (4 * c_lane + t)) & 1u) << 31;
+  const int arow = wm * 8 + (g >> 2);
+  const int bcol = wn * WN + g;
+
+  double acc[2][NC][4];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[r][cc][e] = 0.0;
+
+  for (int kt = 0; kt < ktiles; ++kt) {
+    const uint32_t q = kb_run + kt;
+    const int st = q % kStages;
+    const uint32_t par = (q / kStages) & 1;
+    const int64_t kk0 = static_cast<int64_t>(kt) * kBKQ;
+    double *a_t = sA + st * kMaxTileElems;
+    double *b_t = sB + st * kMaxTileElems;
+    if (!p.tmaA)
+      load_tile_plain<LAYOUT, A_R, A_C>(a_t, p.A, p.a_rows, p.a_cols, p.lda, p.psA,
+                                        TA ? kk0 : i0, TA ? i0 : kk0);
+    if (!p.tmaB)
+      load_tile_plain<LAYOUT, B_R, B_C>(b_t, p.B, p.b_rows, p.b_cols, p.ldb, p.psB,
+                                        TB ? n0 : kk0, TB ? kk0 : n0);
+    bool ok = true;
+    if (any_tma) ok = mbar_wait_bounded(&full[st], par, limit_ns);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicCAS(err_word, 0, QGEMM_ERR_TIMEOUT);
+        for (int r = kt; r < ktiles && r < kt + kStages; ++r) {
+          const uint32_t qq = kb_run + r;
+          mbar_wait_bounded(&full[qq % kStages], (qq / kStages) & 1, limit_ns);
+        }
+      }
+      return false;
+    }
+#pragma unroll 4
+    for (int kk = 0; kk < kBKQ; ++kk) {
+      double a[2][2], b[NC];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int i = arow + 4 * r;
+        a[r][0] = flip_sign(a_t[TA ? tile_idx<LAYOUT, A_R, A_C>(kk, i, compA)
+                                   : tile_idx<LAYOUT, A_R, A_C>(i, kk, compA)], negA);
+        a[r][1] = flip_sign(a_t[TA ? tile_idx<LAYOUT, A_R, A_C>(kk, i + 2, compA)
+                                   : tile_idx<LAYOUT, A_R, A_C>(i + 2, kk, compA)], negA);
+      }
+#pragma unroll
+      for (int cc = 0; cc < NC; ++cc) {
+        const int j = bcol + 8 * cc;
+        b[cc] = b_t[TB ? tile_idx<LAYOUT, B_R, B_C>(j, kk, t) : tile_idx<LAYOUT, B_R, B_C>(kk, j, t)];
+      }
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int cc = 0; cc < NC; ++cc) dmma_16x8x4(acc[r][cc], a[r][0], a[r][1], b[cc]);
+    }
+    __syncthreads();
+    if (tid == 0 && any_tma && kt + kStages < ktiles) issue(kt + kStages);
+  }
+  kb_run += ktiles;
+
+  // epilogue: C <- alpha P + beta C, left products, FP64
+  double la[4], lb[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int s = c_lane ^ j;
+    la[j] = basis_sign(s, j) < 0 ? -p.alpha[s] : p.alpha[s];
+    lb[j] = basis_sign(s, j) < 0 ? -p.beta[s] : p.beta[s];
+  }
+  const int src_base = lane & ~0xC;
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int64_t qi = i0 + arow + 4 * r + 2 * (e >> 1);
+        const int64_t qn = n0 + wn * WN + 8 * cc + 2 * t + (e & 1);
+        const bool inb = qi < p.m && qn < p.n;
+        double P[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) P[j] = __shfl_sync(0xffffffffu, acc[r][cc][e], src_base | (j << 2));
+        double out = la[0] * P[0];
+        out = fma(la[1], P[1], out);
+        out = fma(la[2], P[2], out);
+        out = fma(la[3], P[3], out);
+        double *dst = LAYOUT == QGEMM_INTERLEAVED ? p.C + 4 * (qi + qn * p.ldc) + c_lane
+                                                  : p.C + c_lane * p.psC + qi + qn * p.ldc;
+        if (!p.beta_zero) {
+          const double cin = inb ? *dst : 0.0;
+          double Cq[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) Cq[j] = __shfl_sync(0xffffffffu, cin, src_base | (j << 2));
+#pragma unroll
+          for (int j = 0; j < 4; ++j) out = fma(lb[j], Cq[j], out);
+        }
+        if (inb) *dst = out;
+      }
+  return true;
+}
+
+}  // namespace fp64
+}  // namespace qg

@@ -1,0 +1,561 @@
+// Split-BF16 quaternion GEMM on the fifth-generation tensor cores (tcgen05):
+// device code shared by the single-problem path (split_bf16.cu) and the
+// grouped path (grouped.cu).
+//
+// Real form.  With a = op(A)_{i kappa}, b = op(B)_{kappa n}, the Hamilton
+// product (Sec. 2.1, Eq. quaternion_prod) is linear in a:
+//     (a b)^c = sum_j sign(j, j xor c) a^j b^(j xor c),
+// sign(p, q) the sign of the basis product e_p e_q (Eq. quaternion_alg).  So
+//     C'(m x 4n) = A'(m x 4k) * B'(4k x 4n),
+//     A'[i][4 kappa + j]         = a^j                                (A as stored)
+//     B'[4 kappa + j][4 n + c]   = sign(j, j xor c) b^(j xor c)       (B expanded)
+//     C'[i][4 n + c]             = (op(A) op(B))_{i n}^c
+// which is one real GEMM with exactly the 16 m n k multiplies of the
+// quaternion product; conjugation of A or B only flips signs of A' / B'.
+//
+// Precision.  Each FP32 value x is split into three BF16 terms by
+// round-to-nearest: hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid)
+// (both differences exact in FP32).  The six leading term products
+// hh, hm, mh, hl, mm, lh run on tcgen05.mma kind::f16 (BF16 in, FP32 out in
+// tensor memory); mid*lo, lo*mid and lo*lo (relative size 2^-24) are dropped.
+// The FP32 tensor-memory accumulator is drained every `chunk` k-blocks into a
+// register accumulator (two TMEM buffers, so the MMAs never wait for the
+// drain); the tensor core's in-accumulator additions are biased, so the
+// chunk is short and the register sum takes the rest.  The epilogue forms
+// alpha P and beta C in FP32 and sums them in FP64 before the one rounding.
+//
+// Kernel.  Persistent: each CTA walks tiles blockIdx.x, +gridDim.x, ...; one
+// warp issues TMA loads (3-D boxes: K x rows x term, 64-byte swizzle) into a
+// 3-stage ring, one warp issues the MMAs (M=128, N=256, K=16) into one of two
+// TMEM accumulators and commits them to mbarriers, eight warps drain TMEM and
+// run the epilogue of a tile while the MMAs of the next one proceed.  Ring
+// slots, barrier phases and TMEM buffers are indexed by running counters that
+// continue across tiles.  Every wait is bounded.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace qg {
+namespace split {
+
+// ---------------------------------------------------------------- sizes ---
+constexpr int BM = 128;            // rows of C per tile (TMEM lanes)
+constexpr int BN = 256;            // columns of C' per tile = 64 quaternion columns
+constexpr int BNQ = BN / 4;
+constexpr int BK = 32;             // reals of K per stage (64 bytes: one swizzle row)
+constexpr int STAGES = 3;
+constexpr int TERMS = 3;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;  // warp 0 TMA, warp 1 MMA, 2..9 drain/epilogue
+constexpr uint32_t kATermBytes = BM * BK * 2;  // 8 KB
+constexpr uint32_t kBTermBytes = BN * BK * 2;  // 16 KB
+constexpr uint32_t kStageA = TERMS * kATermBytes;
+constexpr uint32_t kStageB = TERMS * kBTermBytes;
+constexpr uint32_t kStageBytes = kStageA + kStageB;  // 72 KB
+constexpr uint32_t kTmemCols = 2 * BN;               // two accumulator buffers
+constexpr size_t kSmemBytes = 1024 + STAGES * kStageBytes + 256;
+constexpr int kGroupM = 8;                           // row tiles per raster group
+
+// The six kept term products (A term, B term): hh, hm, mh, hl, mm, lh.
+__host__ __device__ constexpr int term_a(int tp) { return tp == 2 || tp == 4 ? 1 : (tp == 5 ? 2 : 0); }
+__host__ __device__ constexpr int term_b(int tp) { return tp == 1 || tp == 4 ? 1 : (tp == 3 ? 2 : 0); }
+
+// ------------------------------------------------------ tcgen05 helpers ---
+// Shared-memory matrix descriptor, K-major, 64-byte swizzle: 8-row groups
+// 512 bytes apart (SBO), leading offset unused, descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFF);
+  d |= static_cast<uint64_t>(1) << 16;                  // LBO (ignored for swizzled K-major)
+  d |= static_cast<uint64_t>(512 >> 4) << 32;           // SBO
+  d |= static_cast<uint64_t>(1) << 46;                  // version
+  d |= static_cast<uint64_t>(4) << 61;                  // SWIZZLE_64B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 D, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4)                                      // D format F32
+         | (1u << 7)                                    // A format BF16
+         | (1u << 10)                                   // B format BF16
+         | (static_cast<uint32_t>(N >> 3) << 17)        // N / 8
+         | (static_cast<uint32_t>(M >> 4) << 24);       // M / 16
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+// 32 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ bool elect_one() {
+  uint32_t pred = 0;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "elect.sync _|p, 0xffffffff;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(pred));
+  return pred != 0;
+}
+
+// --------------------------------------------------------- split helper ---
+struct Split3 {
+  __nv_bfloat16 t[3];
+};
+__device__ __forceinline__ Split3 split3(float x) {
+  Split3 s;
+  s.t[0] = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(s.t[0]);
+  s.t[1] = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(s.t[1]);
+  s.t[2] = __float2bfloat16_rn(r2);
+  return s;
+}
+
+// ----------------------------------------------------------- pre-pass ---
+// One 32 x 32 tile of the op-matrix X (rows r = i for A or n for B; columns
+// kappa), read coalesced from the stored layout through shared memory, split,
+// and written K-major.  For A:  A'_t[r][4 kappa + j]  (row pitch kp).
+// For B:  B'_t[4 r + c][4 kappa + j] = sign(j, j^c) * t(b^(j^c))  (row pitch kp).
+// Columns kappa >= kq up to kp/4 are written as zeros (K padding).
+struct PrepArgs {
+  const float *X;
+  int64_t ld, ps;       // stored leading dimension, plane stride
+  int64_t rows;         // rows of the op-matrix (m for A, n for B)
+  int64_t kq;           // quaternion K
+  int64_t kp;           // padded real K (multiple of BK)
+  int64_t term_stride;  // elements between terms in the output
+  __nv_bfloat16 *out;
+  int layout;
+  int row_contig;       // stored row index == op row (contiguous along r)
+  uint32_t negmask;     // bit j: negate component j of the input (conjugation)
+  int pad;
+};
+
+template <bool IS_B>
+__device__ __forceinline__ void prep_tile(const PrepArgs &p, int64_t rt, int64_t kt,
+                                          float4 (*tile)[33]) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int64_t r0 = rt * 32, k0 = kt * 32;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int a = tx, b = ty + 8 * s;
+    const int rr = p.row_contig ? a : b;
+    const int kk = p.row_contig ? b : a;
+    const int64_t r = r0 + rr, kq = k0 + kk;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r < p.rows && kq < p.kq) {
+      const int64_t sr = p.row_contig ? r : kq, sc = p.row_contig ? kq : r;
+      if (p.layout == QGEMM_INTERLEAVED) {
+        const float *e = p.X + 4 * (sr + sc * p.ld);
+        v = make_float4(e[0], e[1], e[2], e[3]);
+      } else {
+        const float *e = p.X + sr + sc * p.ld;
+        v = make_float4(e[0], e[p.ps], e[2 * p.ps], e[3 * p.ps]);
+      }
+      if (p.negmask & 2u) v.y = -v.y;
+      if (p.negmask & 4u) v.z = -v.z;
+      if (p.negmask & 8u) v.w = -v.w;
+    }
+    tile[kk][rr] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int kk = tx, rr = ty + 8 * s;
+    const int64_t r = r0 + rr, kq = k0 + kk;
+    if (r >= p.rows || 4 * kq >= p.kp) continue;
+    const float4 v = tile[kk][rr];
+    const float comp[4] = {v.x, v.y, v.z, v.w};
+    Split3 sp[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sp[j] = split3(comp[j]);
+    if (!IS_B) {
+#pragma unroll
+      for (int t = 0; t < TERMS; ++t) {
+        __nv_bfloat16 *dst = p.out + t * p.term_stride + r * p.kp + 4 * kq;
+        __align__(8) __nv_bfloat16 w[4] = {sp[0].t[t], sp[1].t[t], sp[2].t[t], sp[3].t[t]};
+        *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(w);
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < TERMS; ++t)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          __align__(8) __nv_bfloat16 w[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int q = j ^ c;
+            const __nv_bfloat16 x = sp[q].t[t];
+            w[j] = basis_sign(j, q) < 0 ? __hneg(x) : x;
+          }
+          __nv_bfloat16 *dst = p.out + t * p.term_stride + (4 * r + c) * p.kp + 4 * kq;
+          *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(w);
+        }
+    }
+  }
+}
+
+// --------------------------------------------------------- GEMM params ---
+// Per-problem parameters of the GEMM kernel.
+struct GemmParams {
+  int64_t m, n;           // quaternion sizes of C
+  int num_kb;             // k-blocks of BK reals (0: C <- beta C)
+  int num_mt, num_nt;     // tiles
+  int layout;
+  int beta_zero;
+  int c_vec4;             // interleaved C 16-byte aligned: float4 access
+  float *C;
+  int64_t ldc, psC;
+  float alpha[4], beta[4];
+};
+
+// Device descriptor of one problem of a grouped batch.
+struct alignas(128) SplitProb {
+  CUtensorMap tmA;  // A' : (kp, m, 3) bf16
+  CUtensorMap tmB;  // B' : (kp, 4n, 3) bf16
+  PrepArgs pa, pb;
+  GemmParams g;
+};
+
+struct SmemCtl {
+  uint64_t full[STAGES];
+  uint64_t empty[STAGES];
+  uint64_t accfull[2];
+  uint64_t accempty[2];
+  uint64_t done;
+  uint32_t tmem_base;
+  int abort;
+};
+
+template <class Err>
+__device__ __forceinline__ void set_abort(SmemCtl *ctl) {
+  atomicCAS(Err::word(), 0, QGEMM_ERR_TIMEOUT);
+  *reinterpret_cast<volatile int *>(&ctl->abort) = 1;
+}
+__device__ __forceinline__ bool aborted(SmemCtl *ctl) {
+  return *reinterpret_cast<volatile int *>(&ctl->abort) != 0;
+}
+// Bounded wait that also gives up as soon as another role has aborted.
+__device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
+                                           SmemCtl *ctl) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (aborted(ctl) || globaltimer_ns() - t0 > limit_ns) return false;
+  }
+}
+
+// Tile t -> problem parameters, tensor maps and tile coordinates.
+template <bool GROUPED>
+__device__ __forceinline__ void tile_of(int t, const GemmParams &single, const CUtensorMap *smA,
+                                        const CUtensorMap *smB, const SplitProb *probs,
+                                        const int4 *tiles, const GemmParams *&g,
+                                        const CUtensorMap *&mA, const CUtensorMap *&mB, int &mt,
+                                        int &nt) {
+  if (GROUPED) {
+    const int4 e = tiles[t];
+    const SplitProb *pr = probs + e.x;
+    g = &pr->g;
+    mA = &pr->tmA;
+    mB = &pr->tmB;
+    mt = e.y;
+    nt = e.z;
+  } else {
+    g = &single;
+    mA = smA;
+    mB = smB;
+    const int per_group = kGroupM * single.num_nt;
+    const int first_m = (t / per_group) * kGroupM;
+    const int gsize = min(single.num_mt - first_m, kGroupM);
+    mt = first_m + (t % per_group) % gsize;
+    nt = (t % per_group) / gsize;
+  }
+}
+
+// Epilogue of one tile for one drain thread: row i, 32 quaternion columns
+// starting at nbase, accumulated P in acc.  out = alpha P + beta C (left
+// products); alpha P and beta C in FP32, their sum in FP64, one rounding.
+__device__ __forceinline__ void epilogue(const GemmParams &g, int64_t i, int64_t nbase,
+                                         const float (&acc)[128]) {
+  if (i >= g.m) return;
+  float sa[4][4], sb[4][4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int s = c ^ j;
+      sa[c][j] = basis_sign(s, j) < 0 ? -g.alpha[s] : g.alpha[s];
+      sb[c][j] = basis_sign(s, j) < 0 ? -g.beta[s] : g.beta[s];
+    }
+#pragma unroll
+  for (int q = 0; q < 32; ++q) {
+    const int64_t nn = nbase + q;
+    if (nn >= g.n) continue;
+    const float P[4] = {acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]};
+    float cin[4] = {0.f, 0.f, 0.f, 0.f};
+    float *dst0;
+    if (g.layout == QGEMM_INTERLEAVED) {
+      dst0 = g.C + 4 * (i + nn * g.ldc);
+      if (!g.beta_zero) {
+        if (g.c_vec4) {
+          const float4 c4 = *reinterpret_cast<const float4 *>(dst0);
+          cin[0] = c4.x; cin[1] = c4.y; cin[2] = c4.z; cin[3] = c4.w;
+        } else {
+#pragma unroll
+          for (int s = 0; s < 4; ++s) cin[s] = dst0[s];
+        }
+      }
+    } else {
+      dst0 = g.C + i + nn * g.ldc;
+      if (!g.beta_zero) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) cin[s] = dst0[s * g.psC];
+      }
+    }
+    float out[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float ap = 0.f, bc = 0.f;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        ap = fmaf(sa[c][j], P[j], ap);
+        bc = fmaf(sb[c][j], cin[j], bc);
+      }
+      out[c] = g.beta_zero ? ap
+                           : static_cast<float>(static_cast<double>(ap) + static_cast<double>(bc));
+    }
+    if (g.layout == QGEMM_INTERLEAVED) {
+      if (g.c_vec4)
+        *reinterpret_cast<float4 *>(dst0) = make_float4(out[0], out[1], out[2], out[3]);
+      else
+#pragma unroll
+        for (int s = 0; s < 4; ++s) dst0[s] = out[s];
+    } else {
+#pragma unroll
+      for (int s = 0; s < 4; ++s) dst0[s * g.psC] = out[s];
+    }
+  }
+}
+
+// Persistent split-BF16 GEMM.  Single problem: tensor maps and parameters
+// are kernel parameters, tiles rasterised in groups of kGroupM row tiles.
+// Grouped: tiles[t] = (problem, row tile, column tile), per-problem maps and
+// parameters in probs.  Err::word() is the device status word.
+template <class Err, bool GROUPED>
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                const GemmParams single, const SplitProb *__restrict__ probs,
+                const int4 *__restrict__ tiles, int ntiles, int chunk, uint64_t limit_ns) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uint32_t raw_addr = smem_u32(smem_raw);
+  unsigned char *ring = smem_raw + ((1024 - (raw_addr & 1023)) & 1023);
+  SmemCtl *ctl = reinterpret_cast<SmemCtl *>(ring + STAGES * kStageBytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&ctl->full[s], 1);
+      mbar_init(&ctl->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&ctl->accfull[b], 1);
+      mbar_init(&ctl->accempty[b], kEpiWarps);
+    }
+    mbar_init(&ctl->done, 1);
+    ctl->abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(&ctl->tmem_base, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ctl->tmem_base;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (elect_one()) {
+      if (!GROUPED) {
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmB);
+      }
+      uint32_t s_run = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const GemmParams *g;
+        const CUtensorMap *mA, *mB;
+        int mt, nt;
+        tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt);
+        const int nkb = g->num_kb;
+        for (int kb = 0; kb < nkb; ++kb, ++s_run) {
+          const int st = s_run % STAGES;
+          if (!wait_phase(&ctl->empty[st], ((s_run / STAGES) & 1) ^ 1, limit_ns, ctl)) {
+            set_abort<Err>(ctl);
+            ok = false;
+            break;
+          }
+          unsigned char *sa = ring + st * kStageBytes;
+          mbar_arrive_expect_tx(&ctl->full[st], kStageBytes);
+          tma_load_3d(sa, mA, &ctl->full[st], kb * BK, mt * BM, 0);
+          tma_load_3d(sa + kStageA, mB, &ctl->full[st], kb * BK, nt * BN, 0);
+        }
+      }
+      if (!ok) {  // let this CTA's copies in flight land before it retires
+        for (uint32_t q = s_run > STAGES ? s_run - STAGES : 0; q < s_run; ++q)
+          mbar_wait_bounded(&ctl->full[q % STAGES], (q / STAGES) & 1, limit_ns);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (elect_one()) {
+      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      const uint32_t ring_addr = smem_u32(ring);
+      uint32_t s_run = 0, c_run = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const GemmParams *g;
+        const CUtensorMap *mA, *mB;
+        int mt, nt;
+        tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt);
+        const int nkb = g->num_kb;
+        for (int kb = 0; kb < nkb && ok; ++c_run) {
+          const int b = c_run & 1;
+          if (!wait_phase(&ctl->accempty[b], ((c_run >> 1) & 1) ^ 1, limit_ns, ctl)) {
+            set_abort<Err>(ctl);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d = tmem + b * BN;
+          const int kb_end = min(nkb, kb + chunk);
+          bool first = true;
+          for (; kb < kb_end; ++kb, ++s_run) {
+            const int st = s_run % STAGES;
+            if (!wait_phase(&ctl->full[st], (s_run / STAGES) & 1, limit_ns, ctl)) {
+              set_abort<Err>(ctl);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = ring_addr + st * kStageBytes;
+            const uint32_t sb = sa + kStageA;
+#pragma unroll
+            for (int ks = 0; ks < BK / 16; ++ks) {
+#pragma unroll
+              for (int tp = 0; tp < 6; ++tp) {
+                const uint64_t ad = smem_desc_sw64(sa + term_a(tp) * kATermBytes + ks * 32);
+                const uint64_t bd = smem_desc_sw64(sb + term_b(tp) * kBTermBytes + ks * 32);
+                umma_bf16(d, ad, bd, idesc, first ? 0u : 1u);
+                first = false;
+              }
+            }
+            umma_commit(&ctl->empty[st]);  // frees the stage when these MMAs finish
+          }
+          if (!ok) break;
+          umma_commit(&ctl->accfull[b]);  // chunk accumulator ready for the drain
+        }
+      }
+      // all MMAs issued by this thread complete before TMEM is released
+      umma_commit(&ctl->done);
+      mbar_wait_bounded(&ctl->done, 0, limit_ns);
+    }
+  } else {
+    // ---------------- drain + epilogue (8 warps) ----------------
+    const int ew = warp - 2;
+    const int quad = warp & 3;   // TMEM lanes 32*quad .. +31 (hardware rule: warp % 4)
+    const int half = ew >> 2;    // columns [128*half, 128*half + 128)
+    const uint32_t lane_base = static_cast<uint32_t>(32 * quad) << 16;
+    uint32_t c_run = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const GemmParams *g;
+      const CUtensorMap *mA, *mB;
+      int mt, nt;
+      tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt);
+      const int nkb = g->num_kb;
+      const int nch = (nkb + chunk - 1) / chunk;
+      float acc[128];
+#pragma unroll
+      for (int i = 0; i < 128; ++i) acc[i] = 0.f;
+      for (int ch = 0; ch < nch; ++ch, ++c_run) {
+        const int b = c_run & 1;
+        if (!wait_phase(&ctl->accfull[b], (c_run >> 1) & 1, limit_ns, ctl)) {
+          set_abort<Err>(ctl);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t base = tmem + lane_base + b * BN + half * 128;
+#pragma unroll
+        for (int piece = 0; piece < 4; ++piece) {
+          float v[32];
+          tmem_ld32(base + piece * 32, v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) acc[piece * 32 + i] += v[i];
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ctl->accempty[b]);
+      }
+      if (!ok) break;
+      epilogue(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane,
+               static_cast<int64_t>(nt) * BNQ + 32 * half, acc);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+}  // namespace split
+}  // namespace qg

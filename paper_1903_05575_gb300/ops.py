@@ -102,6 +102,86 @@ def qgemm_backward(X, W, dY, mb, k, n, dX=None, dW=None, accumulate=False,
     return dX, dW
 
 
+class GroupedBatch:
+    """Many independent problems C_p <- alpha_p op(A_p) op(B_p) + beta_p C_p in
+    one persistent launch (C ABI qgemm_grouped_prepare / qgemm_grouped_launch).
+
+    problems: sequence of dicts with keys opA, opB, m, n, k, alpha, beta, A, B,
+    C (tensors of one dtype and layout).  prepare() runs once (not during
+    graph capture); launch() only resets a counter and launches, so it can be
+    captured in a CUDA graph and replayed.  The tensors must stay alive.
+    """
+
+    def __init__(self, problems, layout="interleaved", ws=None, stream=None):
+        import ctypes
+
+        from . import autotune
+        autotune.ensure_plan_loaded()
+        self.problems = list(problems)
+        if not self.problems:
+            raise ValueError("empty batch")
+        self.layout = layout
+        self.prec = precision_of(self.problems[0]["C"].dtype)
+        arr = (_abi.QgemmProblem * len(self.problems))()
+        for i, p in enumerate(self.problems):
+            q = arr[i]
+            q.opA, q.opB = _abi.OP[p["opA"]], _abi.OP[p["opB"]]
+            q.m, q.n, q.k = p["m"], p["n"], p["k"]
+            for s in range(4):
+                q.alpha[s] = float(p["alpha"][s])
+                q.beta[s] = float(p["beta"][s])
+            for name in ("A", "B", "C"):
+                X = p[name]
+                ld, ps, _ = geometry(X, layout)
+                setattr(q, name, X.data_ptr())
+                setattr(q, "ld" + name.lower(), ld)
+                setattr(q, "ps" + name, ps)
+        self._arr = arr
+        L = _abi.lib()
+        n = len(self.problems)
+        need = L.qgemm_grouped_workspace_bytes(arr, n, _abi.LAYOUT[layout],
+                                               _abi.PRECISION[self.prec])
+        if need == 0:
+            raise _abi.QgemmError(_abi.ERR_UNSUPPORTED, "qgemm_grouped_workspace_bytes")
+        dev = self.problems[0]["C"].device
+        self.ws = ws if ws is not None else torch.empty(need, dtype=torch.uint8, device=dev)
+        self.plan = _abi.QgemmGroupedPlan()
+        rc = L.qgemm_grouped_prepare(arr, n, _abi.LAYOUT[layout], _abi.PRECISION[self.prec],
+                                     self.ws.data_ptr(), self.ws.numel(), _stream_handle(stream),
+                                     ctypes.byref(self.plan))
+        _abi.check(rc, "qgemm_grouped_prepare")
+
+    def launch(self, stream=None):
+        import ctypes
+        rc = _abi.lib().qgemm_grouped_launch(ctypes.byref(self.plan), _stream_handle(stream))
+        _abi.check(rc, "qgemm_grouped_launch")
+
+
+def set_tile_table(table, precision="fp64"):
+    """Install a per-bucket tile-shape table (None restores the default).  An
+    explicit table takes precedence over a stored autotuner plan."""
+    import ctypes
+
+    from . import autotune
+    autotune._loaded = True
+    L = _abi.lib()
+    if table is None:
+        rc = L.qgemm_grouped_set_tile_table(_abi.PRECISION[precision], None, 0)
+    else:
+        arr = (ctypes.c_int32 * len(table))(*[int(x) for x in table])
+        rc = L.qgemm_grouped_set_tile_table(_abi.PRECISION[precision], arr, len(table))
+    _abi.check(rc, "qgemm_grouped_set_tile_table")
+
+
+def tile_info():
+    """(shapes [(rows, cols)], number of buckets, bucket edges)."""
+    import ctypes
+    ns, nb = ctypes.c_int32(0), ctypes.c_int32(0)
+    rows, cols, edges = (ctypes.c_int32 * 8)(), (ctypes.c_int32 * 8)(), (ctypes.c_int32 * 4)()
+    _abi.lib().qgemm_grouped_tile_info(ctypes.byref(ns), rows, cols, ctypes.byref(nb), edges)
+    return ([(rows[i], cols[i]) for i in range(ns.value)], nb.value, list(edges))
+
+
 def last_device_error():
     return _abi.lib().qgemm_get_last_device_error()
 
