@@ -60,6 +60,9 @@ def _bind(path):
                                          ctypes.c_int, ctypes.POINTER(i64),
                                          ctypes.POINTER(i64), i64, dp, ctypes.c_int]
     lib.oracle_qgemm_entries.restype = ctypes.c_int
+    lib.oracle_qherk.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, ctypes.c_double, dp, i64,
+                                 i64, ctypes.c_double, dp, i64, i64, ctypes.c_int, ctypes.c_int]
+    lib.oracle_qherk.restype = ctypes.c_int
     lib.oracle_max_threads.argtypes = []
     lib.oracle_max_threads.restype = ctypes.c_int
     return lib
@@ -152,3 +155,18 @@ def qgemm_entries(opA, opB, m, n, k, alpha, A, B, beta, C, rows, cols,
     if rc != 0:
         raise ValueError("oracle_qgemm_entries returned %d" % rc)
     return out
+
+
+def qherk(uplo, trans, n, k, alpha, A, beta, C, layout="interleaved", nthreads=0, lib=None):
+    """Hermitian rank-k update on one triangle of C, in place (real alpha, beta):
+    trans N: C <- alpha A A^H + beta C;  trans H: C <- alpha A^H A + beta C."""
+    lib = lib or _load()
+    for X in (A, C):
+        _check(X)
+    lda, psA, _ = geometry(A, layout)
+    ldc, psC, _ = geometry(C, layout)
+    rc = lib.oracle_qherk({"L": 0, "U": 1}[uplo], OPS[trans], n, k, float(alpha), _dptr(A), lda,
+                          psA, float(beta), _dptr(C), ldc, psC, LAYOUTS[layout], int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_qherk returned %d" % rc)
+    return C

@@ -249,6 +249,59 @@ int oracle_qgemm_entries(int opA, int opB, int64_t m, int64_t n, int64_t k,
     return 0;
 }
 
+/*
+ * Hermitian rank-k update, the quaternion analogue of BLAS xHERK: the kernels
+ * of Sec. 3 serve rank-k updates as well as GEMM (Sec. 3, opening remarks),
+ * and Hermiticity Q = Q^H is defined in Sec. 2.2.
+ *
+ *   trans = N:  C <- alpha A A^H + beta C      (A is n x k)
+ *   trans = H:  C <- alpha A^H A + beta C      (A is k x n)
+ *
+ * alpha and beta are real.  Only the triangle uplo (0 lower: row >= column,
+ * 1 upper: row <= column) of C is read and written; the vector parts of the
+ * diagonal of C are taken as zero on input and set to zero on output (the
+ * diagonal of a Hermitian matrix is real).  Each entry is the plain sum over
+ * kappa of op(A)_{i kappa} conj(op(A)_{j kappa}), in increasing kappa order.
+ */
+int oracle_qherk(int uplo, int trans, int64_t n, int64_t k, double alpha,
+                 const double *A, int64_t lda, int64_t psA, double beta,
+                 double *C, int64_t ldc, int64_t psC, int layout, int nthreads)
+{
+    if (n < 0 || k < 0) return -1;
+    if (uplo != 0 && uplo != 1) return -1;
+    if (trans != ORACLE_OP_N && trans != ORACLE_OP_H) return -1;
+    if (layout != ORACLE_INTERLEAVED && layout != ORACLE_SPLIT_PLANES) return -1;
+    const int read_c = beta != 0.0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t j = 0; j < n; ++j) {
+        const int64_t i_lo = uplo == 0 ? j : 0, i_hi = uplo == 0 ? n : j + 1;
+        for (int64_t i = i_lo; i < i_hi; ++i) {
+            double P[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int64_t kap = 0; kap < k; ++kap) {
+                double a[4], b[4], ab[4];
+                /* op(A)_{i kappa} and conj(op(A)_{j kappa}) = (op(A)^H)_{kappa j} */
+                load_op(A, lda, psA, layout, trans, i, kap, a);
+                load_op(A, lda, psA, layout, trans, j, kap, b);
+                conjugate(b);
+                oracle_hamilton(a, b, ab);
+                P[0] += ab[0]; P[1] += ab[1]; P[2] += ab[2]; P[3] += ab[3];
+            }
+            double cin[4] = {0.0, 0.0, 0.0, 0.0}, out[4];
+            if (read_c) load_stored(C, ldc, psC, layout, i, j, cin);
+            for (int s = 0; s < 4; ++s) out[s] = alpha * P[s] + beta * cin[s];
+            /* diagonal: the vector parts of C are taken as zero and written as zero */
+            if (i == j) out[1] = out[2] = out[3] = 0.0;
+            store_stored(C, ldc, psC, layout, i, j, out);
+        }
+    }
+    return 0;
+}
+
 /* Number of OpenMP threads the oracle would use by default. */
 int oracle_max_threads(void)
 {

@@ -238,9 +238,61 @@ def pin_entries_match_full(lib):
     return True
 
 
+def _hermitian_full(T, uplo):
+    """Full Hermitian matrix from the uplo triangle of T (n, n, 4) components,
+    diagonal vector parts zeroed."""
+    n = T.shape[0]
+    F = np.zeros_like(T)
+    for i in range(n):
+        for j in range(n):
+            src = (i, j) if (i >= j) == (uplo == "L") or i == j else (j, i)
+            v = T[src].copy()
+            if src != (i, j):
+                v[1:] = -v[1:]
+            F[i, j] = v
+    for i in range(n):
+        F[i, i, 1:] = 0.0
+    return F
+
+
+def pin_herk_vs_complex(lib):
+    """Hermitian rank-k update (Sec. 2.2 Hermiticity; rank-k updates of Sec. 3):
+    the triangle equals alpha op(A) op(A)^H + beta C computed through the
+    complex representation (numpy), exactly on small integers; the other
+    triangle is untouched and the diagonal is real."""
+    n, k = 5, 4
+    for layout in qsynth.LAYOUTS:
+        for uplo in ("L", "U"):
+            for trans in ("N", "H"):
+                ra, ca = (n, k) if trans == "N" else (k, n)
+                A = qsynth.small_int(ra, ca, 91, layout, ld=ra + 1)
+                C = qsynth.small_int(n, n, 92, layout, ld=n + 2)
+                alpha, beta = 3.0, -2.0
+                got = C.copy()
+                orc.qherk(uplo, trans, n, k, alpha, A, beta, got, layout=layout, lib=lib)
+                Ac = qsynth.components(A, ra, layout)
+                Cc = qsynth.components(C, n, layout)
+                Ao = qref.apply_op(Ac, trans)
+                Cf = _hermitian_full(Cc, uplo)
+                want = qref.from_complex(alpha * (qref.to_complex(Ao) @ qref.to_complex(Ao).conj().T)
+                                         + beta * qref.to_complex(Cf), n, n)
+                G = qsynth.components(got, n, layout)
+                for i in range(n):
+                    for j in range(n):
+                        in_tri = (i >= j) if uplo == "L" else (i <= j)
+                        if in_tri and not np.array_equal(G[i, j], want[i, j]):
+                            return False
+                        if not in_tri and not np.array_equal(G[i, j], Cc[i, j]):
+                            return False
+                    if np.any(G[i, i, 1:] != 0.0):
+                        return False
+    return True
+
+
 PINS = [pin_basis_table, pin_worked_products, pin_norm_multiplicative, pin_complex_subalgebra,
         pin_scalar_complex_rep, pin_gemm_vs_complex, pin_conj_transpose_identity,
-        pin_associative, pin_scalar_side, pin_blas_conventions, pin_entries_match_full]
+        pin_associative, pin_scalar_side, pin_blas_conventions, pin_entries_match_full,
+        pin_herk_vs_complex]
 
 
 def failing_pins(lib, pins=PINS):
@@ -292,6 +344,11 @@ MUTATIONS = {
                          "oracle_hamilton(b, a, ab);\n                    double *p"),
     "beta_read_when_zero": ("const int read_c = !is_zero(beta);\n#ifdef _OPENMP\n    if (nthreads > 0) omp_set_num_threads(nthreads);\n#else\n    (void)nthreads;\n#endif\n    int status",
                             "const int read_c = 1;\n#ifdef _OPENMP\n    if (nthreads > 0) omp_set_num_threads(nthreads);\n#else\n    (void)nthreads;\n#endif\n    int status"),
+    "herk_no_conjugate": ("conjugate(b);\n                oracle_hamilton(a, b, ab);",
+                          "oracle_hamilton(a, b, ab);"),
+    "herk_diag_not_real": ("if (i == j) out[1] = out[2] = out[3] = 0.0;", "(void)0;"),
+    "herk_operands_swapped": ("load_op(A, lda, psA, layout, trans, i, kap, a);\n                load_op(A, lda, psA, layout, trans, j, kap, b);",
+                              "load_op(A, lda, psA, layout, trans, j, kap, a);\n                load_op(A, lda, psA, layout, trans, i, kap, b);"),
     "plane_stride_wrong": ("q[0] = e[0]; q[1] = e[ps]; q[2] = e[2 * ps]; q[3] = e[3 * ps];",
                            "q[0] = e[0]; q[1] = e[ps]; q[2] = e[3 * ps]; q[3] = e[2 * ps];"),
 }
