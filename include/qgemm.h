@@ -76,6 +76,9 @@ extern "C" {
 #define QGEMM_INTERLEAVED 0
 #define QGEMM_SPLIT_PLANES 1
 
+#define QGEMM_LOWER 0
+#define QGEMM_UPPER 1
+
 #define QGEMM_FP64 0
 #define QGEMM_FP32_SPLIT_BF16 1
 
@@ -237,6 +240,30 @@ int qgemm_grouped_tile_info(int32_t *num_shapes, int32_t *shape_m, int32_t *shap
                             int32_t *num_buckets, int32_t *edges);
 
 /*
+ * qherk: Hermitian rank-k update on one triangle of C (the quaternion xHERK;
+ * the paper notes its GEMM kernels also serve rank-k updates, Sec. 3, and
+ * defines Hermiticity Q = Q^H in Sec. 2.2):
+ *     trans = QGEMM_OP_N:  C <- alpha A A^H + beta C     (A is n x k)
+ *     trans = QGEMM_OP_H:  C <- alpha A^H A + beta C     (A is k x n)
+ * alpha and beta are REAL.  Only the triangle `uplo` (QGEMM_LOWER: row >=
+ * column; QGEMM_UPPER: row <= column) of C is read and written; the vector
+ * parts of C's diagonal are taken as zero and written as zero.  It runs the
+ * same kernels as qgemm() with op(B) = op(A)^H read from A itself, skipping
+ * tiles outside the triangle.  Arguments, in order for the -i return:
+ *   1 uplo, 2 trans, 3 n, 4 k, 5 alpha, 6 A, 7 lda, 8 psA, 9 beta, 10 C,
+ *   11 ldc, 12 psC, 13 layout, 14 precision, 15 workspace, 16 workspace_bytes,
+ *   17 stream; layouts, precisions and workspace as in qgemm().
+ */
+int qherk(int uplo, int trans, int64_t n, int64_t k, double alpha,
+          const void *A, int64_t lda, int64_t psA, double beta,
+          void *C, int64_t ldc, int64_t psC, int layout, int precision,
+          void *workspace, size_t workspace_bytes, void *stream);
+
+/* Workspace qherk() needs (0 for QGEMM_FP64). */
+size_t qherk_workspace_bytes(int uplo, int trans, int64_t n, int64_t k,
+                             int layout, int precision);
+
+/*
  * qgemm_backward: gradients of a quaternion linear map Y = X W, with
  * X (mb x k), W (k x n), Y (mb x n) stored untransposed.  With the real inner
  * product <P, Q> = Re tr(P^H Q) = sum of component products, and
@@ -265,6 +292,10 @@ size_t qgemm_backward_workspace_bytes(int64_t mb, int64_t k, int64_t n,
  * Returns QGEMM_SUCCESS or QGEMM_ERR_TIMEOUT. */
 int qgemm_get_last_device_error(void);
 
+/* Name of the CUDA error behind the most recent QGEMM_ERR_CUDA returned by a
+ * launch in this process ("no error" if none); a diagnostic aid. */
+const char *qgemm_last_cuda_error(void);
+
 /* Static description of a status code. */
 const char *qgemm_status_string(int status);
 
@@ -280,7 +311,10 @@ int qgemm_debug_unsatisfied_wait(uint64_t limit_ns, void *stream);
  * Throughput microbenchmarks of the device's arithmetic pipes (no paper
  * counterpart; they supply the roofline denominators).  which:
  *   0 FP64 tensor (DMMA m16n8k4)   1 FP64 FMA (DFMA)   2 FP32 FMA (FFMA)
- *   3 BF16 tensor (tcgen05.mma kind::f16, 128x256x16, FP32 accumulate)
+ *   3 BF16 tensor (tcgen05.mma kind::f16, 128x256x16, FP32 accumulate),
+ *     zero operands
+ *   4, 5, 6 the same instruction at N = 256, 128, 64 on operands holding
+ *     integers in [-127, 127]
  * Runs for roughly `seconds` and writes the achieved TFLOP/s (2 per FMA).
  */
 int qgemm_probe_peak(int which, double seconds, double *tflops, void *stream);

@@ -58,11 +58,15 @@ SIGNATURES = {
     "qgemm_grouped_launch": (i32, [ctypes.POINTER(QgemmGroupedPlan), vp]),
     "qgemm_grouped_set_tile_table": (i32, [i32, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
     "qgemm_grouped_tile_info": (i32, [ctypes.POINTER(ctypes.c_int32)] * 5),
+    "qherk": (i32, [i32, i32, i64, i64, ctypes.c_double, vp, i64, i64, ctypes.c_double, vp, i64,
+                    i64, i32, i32, vp, sz, vp]),
+    "qherk_workspace_bytes": (sz, [i32, i32, i64, i64, i32, i32]),
     "qgemm_backward": (i32, [i64, i64, i64, vp, i64, i64, vp, i64, i64, vp, i64, i64,
                              vp, i64, i64, vp, i64, i64, i32, i32, i32, vp, sz, vp]),
     "qgemm_backward_workspace_bytes": (sz, [i64, i64, i64, i32, i32]),
     "qgemm_get_last_device_error": (i32, []),
     "qgemm_status_string": (ctypes.c_char_p, [i32]),
+    "qgemm_last_cuda_error": (ctypes.c_char_p, []),
     "qgemm_debug_unsatisfied_wait": (i32, [ctypes.c_uint64, vp]),
     "qgemm_probe_peak": (i32, [i32, ctypes.c_double, dp, vp]),
     "qgemm_version": (ctypes.c_char_p, []),
@@ -104,7 +108,10 @@ def status_string(rc):
 class QgemmError(RuntimeError):
     def __init__(self, rc, what=""):
         self.rc = rc
-        super().__init__("%s failed: %d (%s)" % (what or "qgemm", rc, status_string(rc)))
+        detail = status_string(rc)
+        if rc == ERR_CUDA:
+            detail += ": " + lib().qgemm_last_cuda_error().decode()
+        super().__init__("%s failed: %d (%s)" % (what or "qgemm", rc, detail))
 
 
 def check(rc, what=""):

@@ -1,5 +1,6 @@
 // C ABI entry points: argument validation (BLAS rules), quick returns and
 // dispatch to the kernels.  Nothing here computes on the host.
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -70,6 +71,7 @@ int validate_gemm(int opA, int opB, int64_t m, int64_t n, int64_t k, const doubl
   d->psc = psC;
   d->layout = layout;
   d->beta_zero = is_zero4(beta);
+  d->tri = 0;
   return 0;
 }
 
@@ -86,6 +88,18 @@ EncodeTiledFn encode_tiled_fn() {
   });
   return fn;
 }
+
+namespace {
+std::atomic<int> g_last_cuda_error{0};
+}  // namespace
+
+int record_cuda_error(cudaError_t e) {
+  if (e == cudaSuccess) return QGEMM_SUCCESS;
+  g_last_cuda_error.store(static_cast<int>(e));
+  return QGEMM_ERR_CUDA;
+}
+
+int launch_status() { return record_cuda_error(cudaGetLastError()); }
 
 uint64_t wait_limit_ns() {
   static uint64_t v = [] {
@@ -192,6 +206,54 @@ size_t qgemm_workspace_bytes(int opA, int opB, int64_t m, int64_t n, int64_t k, 
   return b;
 }
 
+int qherk(int uplo, int trans, int64_t n, int64_t k, double alpha, const void *A, int64_t lda,
+          int64_t psA, double beta, void *C, int64_t ldc, int64_t psC, int layout, int precision,
+          void *workspace, size_t workspace_bytes, void *stream) {
+  if (uplo != QGEMM_LOWER && uplo != QGEMM_UPPER) return -1;
+  if (trans != QGEMM_OP_N && trans != QGEMM_OP_H) return -2;
+  if (n < 0) return -3;
+  if (k < 0) return -4;
+  // C <- alpha op(A) op(A)^H + beta C  as the product op(A) * (op(A))^H:
+  // op(B) is the conjugate transpose of op(A), on the same matrix.
+  const int opB = trans == QGEMM_OP_N ? QGEMM_OP_H : QGEMM_OP_N;
+  const double al[4] = {alpha, 0.0, 0.0, 0.0}, be[4] = {beta, 0.0, 0.0, 0.0};
+  GemmDesc d;
+  int rc = validate_gemm(trans, opB, n, n, k, al, A, lda, psA, A, lda, psA, be, C, ldc, psC,
+                         layout, precision, &d);
+  if (rc) {
+    // qgemm positions -> qherk positions
+    static const int map[22] = {0, 2, 2, 3, 3, 4, 5, 6, 7, 8, 6, 7, 8, 9, 10, 11, 12, 13, 14,
+                                15, 16, 17};
+    const int pos = -rc;
+    return (pos >= 1 && pos <= 21) ? -map[pos] : rc;
+  }
+  d.tri = uplo == QGEMM_LOWER ? 1 : 2;
+  size_t need = 0;
+  if (precision == QGEMM_FP32_SPLIT_BF16 && d.k > 0) {
+    rc = split_workspace_bytes(d, &need);
+    if (rc) return rc;
+  }
+  if (need > 0) {
+    if (workspace == nullptr || reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return -15;
+    if (workspace_bytes < need) return -16;
+  }
+  if (n == 0) return QGEMM_SUCCESS;
+  rc = device_ready();
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (d.k == 0) return launch_herk_scale(d, precision == QGEMM_FP64, s);
+  if (precision == QGEMM_FP64) return launch_fp64_gemm(d, s);
+  return launch_split_gemm(d, workspace, workspace_bytes, s);
+}
+
+size_t qherk_workspace_bytes(int uplo, int trans, int64_t n, int64_t k, int layout,
+                             int precision) {
+  (void)uplo;
+  if (trans != QGEMM_OP_N && trans != QGEMM_OP_H) return 0;
+  return qgemm_workspace_bytes(trans, trans == QGEMM_OP_N ? QGEMM_OP_H : QGEMM_OP_N, n, n, k,
+                               layout, precision);
+}
+
 size_t qgemm_backward_workspace_bytes(int64_t mb, int64_t k, int64_t n, int layout,
                                       int precision) {
   size_t a = qgemm_workspace_bytes(QGEMM_OP_N, QGEMM_OP_H, mb, k, n, layout, precision);
@@ -273,7 +335,7 @@ int qgemm_debug_unsatisfied_wait(uint64_t limit_ns, void *stream) {
 }
 
 int qgemm_probe_peak(int which, double seconds, double *tflops, void *stream) {
-  if (which < 0 || which > 3) return -1;
+  if (which < 0 || which > 6) return -1;
   if (!(seconds > 0.0) || seconds > 60.0) return -2;
   if (tflops == nullptr) return -3;
   int rc = device_ready();
@@ -282,5 +344,9 @@ int qgemm_probe_peak(int which, double seconds, double *tflops, void *stream) {
 }
 
 const char *qgemm_version(void) { return "gb300-qgemm 0.1"; }
+
+const char *qgemm_last_cuda_error(void) {
+  return cudaGetErrorString(static_cast<cudaError_t>(g_last_cuda_error.load()));
+}
 
 }  // extern "C"

@@ -36,7 +36,7 @@ struct Fp64Args {
   uint64_t limit_ns;
 };
 
-template <int LAYOUT, bool TA, bool TB>
+template <int LAYOUT, bool TA, bool TB, int BMQ = kBMQ, int BNQ = kBNQ>
 __global__ void __launch_bounds__(kThreads)
     fp64_qgemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, const Fp64Args p) {
@@ -53,16 +53,17 @@ __global__ void __launch_bounds__(kThreads)
   __syncthreads();
   // grouped rasterisation: runs of kGroupM row-tiles share their B column
   // panels in L2 while they sweep the columns
-  const int64_t tiles_m = (p.op.m + kBMQ - 1) / kBMQ, tiles_n = (p.op.n + kBNQ - 1) / kBNQ;
+  const int64_t tiles_m = (p.op.m + BMQ - 1) / BMQ, tiles_n = (p.op.n + BNQ - 1) / BNQ;
   const int64_t tid_lin = static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x;
   const int64_t per_group = kGroupM * tiles_n;
   const int64_t first_m = (tid_lin / per_group) * kGroupM;
   const int64_t gsize = min(tiles_m - first_m, static_cast<int64_t>(kGroupM));
-  const int64_t i0 = (first_m + (tid_lin % per_group) % gsize) * kBMQ;
-  const int64_t n0 = ((tid_lin % per_group) / gsize) * kBNQ;
+  const int64_t i0 = (first_m + (tid_lin % per_group) % gsize) * BMQ;
+  const int64_t n0 = ((tid_lin % per_group) / gsize) * BNQ;
+  if (fp64::tile_outside(p.op.tri, i0, n0, BMQ, BNQ)) return;
   uint32_t kb_run = 0;
-  fp64::tile<LAYOUT, TA, TB, kBMQ, kBNQ>(p.op, &tmA, &tmB, sA, sB, full, kb_run, i0, n0,
-                                         p.limit_ns, &g_fp64_error);
+  fp64::tile<LAYOUT, TA, TB, BMQ, BNQ>(p.op, &tmA, &tmB, sA, sB, full, kb_run, i0, n0,
+                                       p.limit_ns, &g_fp64_error);
 }
 
 // C <- beta C (k == 0 or alpha == 0), or C <- 0 when beta == 0.
@@ -98,10 +99,27 @@ __global__ void scale_kernel(T *C, int64_t m, int64_t n, int64_t ldc, int64_t ps
   }
 }
 
-template <int LAYOUT, bool TA, bool TB>
+// Hermitian rank-k update with k == 0 or alpha == 0: C <- beta C on one
+// triangle (beta real), the diagonal's vector parts set to zero.
+template <typename T, int LAYOUT>
+__global__ void herk_scale_kernel(T *C, int64_t n, int64_t ldc, int64_t psC, double beta, int tri) {
+  const int64_t total = n * n;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e % n, j = e / n;
+    if ((tri == 1 && i < j) || (tri == 2 && i > j)) continue;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      T *q = LAYOUT == QGEMM_INTERLEAVED ? C + 4 * (i + j * ldc) + s : C + s * psC + i + j * ldc;
+      *q = (beta == 0.0 || (i == j && s != 0)) ? T(0) : static_cast<T>(beta * static_cast<double>(*q));
+    }
+  }
+}
+
+template <int LAYOUT, bool TA, bool TB, int BMQ = kBMQ, int BNQ = kBNQ>
 int launch_typed(const CUtensorMap &ta, const CUtensorMap &tb, const Fp64Args &args, dim3 grid,
                  cudaStream_t stream) {
-  auto kern = fp64_qgemm_kernel<LAYOUT, TA, TB>;
+  auto kern = fp64_qgemm_kernel<LAYOUT, TA, TB, BMQ, BNQ>;
   static bool attr_set[64];  // per instantiation and device; benign race (same value)
   int dev = 0;
   cudaGetDevice(&dev);
@@ -115,8 +133,7 @@ int launch_typed(const CUtensorMap &ta, const CUtensorMap &tb, const Fp64Args &a
     attr_set[dev] = true;
   }
   kern<<<grid, kThreads, kSmemBytes, stream>>>(ta, tb, args);
-  if (cudaGetLastError() != cudaSuccess) return QGEMM_ERR_CUDA;
-  return QGEMM_SUCCESS;
+  return launch_status();
 }
 
 }  // namespace
@@ -182,6 +199,7 @@ fp64::Operands fp64_operands(const GemmDesc &d) {
   }
   a.negmask = block_neg_mask(op_conj(d.opA), op_conj(d.opB));
   a.beta_zero = d.beta_zero ? 1 : 0;
+  a.tri = d.tri;
   return a;
 }
 
@@ -190,15 +208,24 @@ int launch_fp64_gemm(const GemmDesc &d, cudaStream_t stream) {
   a.op = fp64_operands(d);
   a.limit_ns = wait_limit_ns();
   const bool ta = op_trans(d.opA), tb = op_trans(d.opB);
+  // 32 x 32 quaternion tiles, or 16 x 16 when 32 x 32 would give fewer than
+  // about 32 waves of the 2 CTAs per SM that fit (the last, partial wave
+  // idles the FP64 pipes of the SMs it leaves out: 16% at 1024^3)
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t big = ((d.m + kBMQ - 1) / kBMQ) * ((d.n + kBNQ - 1) / kBNQ);
+  const bool small = big < 32LL * 2 * sms;
+  const int bm = small ? 16 : kBMQ, bn = small ? 16 : kBNQ;
   CUtensorMap tmA, tmB;
   std::memset(&tmA, 0, sizeof(tmA));
   std::memset(&tmB, 0, sizeof(tmB));
-  a.op.tmaA = encode_fp64_operand(&tmA, d.A, d.layout, ta ? kBKQ : kBMQ, ta ? kBMQ : kBKQ) ? 1 : 0;
-  a.op.tmaB = encode_fp64_operand(&tmB, d.B, d.layout, tb ? kBNQ : kBKQ, tb ? kBKQ : kBNQ) ? 1 : 0;
-  const int64_t gx = (d.m + kBMQ - 1) / kBMQ, gy = (d.n + kBNQ - 1) / kBNQ;
+  a.op.tmaA = encode_fp64_operand(&tmA, d.A, d.layout, ta ? kBKQ : bm, ta ? bm : kBKQ) ? 1 : 0;
+  a.op.tmaB = encode_fp64_operand(&tmB, d.B, d.layout, tb ? bn : kBKQ, tb ? kBKQ : bn) ? 1 : 0;
+  const int64_t gx = (d.m + bm - 1) / bm, gy = (d.n + bn - 1) / bn;
   if (gx > 0x7fffffff || gy > 65535) return QGEMM_ERR_UNSUPPORTED;
   dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy));
-  const int key = (d.layout << 2) | (ta << 1) | tb;
+  const int key = (small ? 8 : 0) | (d.layout << 2) | (ta << 1) | tb;
   switch (key) {
     case 0: return launch_typed<0, false, false>(tmA, tmB, a, grid, stream);
     case 1: return launch_typed<0, false, true>(tmA, tmB, a, grid, stream);
@@ -207,7 +234,15 @@ int launch_fp64_gemm(const GemmDesc &d, cudaStream_t stream) {
     case 4: return launch_typed<1, false, false>(tmA, tmB, a, grid, stream);
     case 5: return launch_typed<1, false, true>(tmA, tmB, a, grid, stream);
     case 6: return launch_typed<1, true, false>(tmA, tmB, a, grid, stream);
-    default: return launch_typed<1, true, true>(tmA, tmB, a, grid, stream);
+    case 7: return launch_typed<1, true, true>(tmA, tmB, a, grid, stream);
+    case 8: return launch_typed<0, false, false, 16, 16>(tmA, tmB, a, grid, stream);
+    case 9: return launch_typed<0, false, true, 16, 16>(tmA, tmB, a, grid, stream);
+    case 10: return launch_typed<0, true, false, 16, 16>(tmA, tmB, a, grid, stream);
+    case 11: return launch_typed<0, true, true, 16, 16>(tmA, tmB, a, grid, stream);
+    case 12: return launch_typed<1, false, false, 16, 16>(tmA, tmB, a, grid, stream);
+    case 13: return launch_typed<1, false, true, 16, 16>(tmA, tmB, a, grid, stream);
+    case 14: return launch_typed<1, true, false, 16, 16>(tmA, tmB, a, grid, stream);
+    default: return launch_typed<1, true, true, 16, 16>(tmA, tmB, a, grid, stream);
   }
 }
 
@@ -235,7 +270,30 @@ int launch_scale(const GemmDesc &d, bool fp64, cudaStream_t stream) {
       scale_kernel<float, 1><<<blocks, threads, 0, stream>>>(C, d.m, d.n, d.ldc, d.psc, b[0], b[1],
                                                              b[2], b[3], bz);
   }
-  return cudaGetLastError() == cudaSuccess ? QGEMM_SUCCESS : QGEMM_ERR_CUDA;
+  return launch_status();
+}
+
+int launch_herk_scale(const GemmDesc &d, bool fp64, cudaStream_t stream) {
+  const int64_t total = d.m * d.m;
+  const int threads = 256;
+  int64_t blocks = (total + threads - 1) / threads;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) return QGEMM_SUCCESS;
+  const double be = d.beta[0];
+  if (fp64) {
+    double *C = static_cast<double *>(d.C);
+    if (d.layout == QGEMM_INTERLEAVED)
+      herk_scale_kernel<double, 0><<<blocks, threads, 0, stream>>>(C, d.m, d.ldc, d.psc, be, d.tri);
+    else
+      herk_scale_kernel<double, 1><<<blocks, threads, 0, stream>>>(C, d.m, d.ldc, d.psc, be, d.tri);
+  } else {
+    float *C = static_cast<float *>(d.C);
+    if (d.layout == QGEMM_INTERLEAVED)
+      herk_scale_kernel<float, 0><<<blocks, threads, 0, stream>>>(C, d.m, d.ldc, d.psc, be, d.tri);
+    else
+      herk_scale_kernel<float, 1><<<blocks, threads, 0, stream>>>(C, d.m, d.ldc, d.psc, be, d.tri);
+  }
+  return launch_status();
 }
 
 int fp64_take_device_error() {

@@ -41,7 +41,16 @@ struct Operands {
   double alpha[4], beta[4];
   uint32_t negmask;
   int tmaA, tmaB, beta_zero;
+  int tri;  // 0 full; 1 lower (row >= col) only; 2 upper; diagonal written real
 };
+
+// True when the tile at quaternion offset (i0, n0) of size BMQ x BNQ has no
+// element in the stored triangle.
+__device__ __forceinline__ bool tile_outside(int tri, int64_t i0, int64_t n0, int bm, int bn) {
+  if (tri == 1) return i0 + bm - 1 < n0;
+  if (tri == 2) return n0 + bn - 1 < i0;
+  return false;
+}
 
 // Shared-memory index of component s of stored element (r, c) of a tile with
 // R stored rows and CC stored columns (the TMA box order).
@@ -113,9 +122,12 @@ __device__ bool tile(const Operands &p, const CUtensorMap *tmA, const CUtensorMa
   const int g = lane >> 2, t = lane & 3;
   const int wm = warp % WARPS_M, wn = warp / WARPS_M;
   const int ktiles = static_cast<int>((p.k + kBKQ - 1) / kBKQ);
-  const bool any_tma = p.tmaA || p.tmaB;
   const uint32_t tx_bytes = (p.tmaA ? kABytes : 0u) + (p.tmaB ? kBBytes : 0u);
 
+  // Every k-block arrives on its ring slot's barrier, with the TMA byte count
+  // (0 when both operands use plain loads): barrier phases then follow the
+  // running k-block count even when a persistent CTA mixes TMA and
+  // plain-load problems.
   auto issue = [&](int kt) {
     const uint32_t q = kb_run + kt;
     const int st = q % kStages;
@@ -124,7 +136,7 @@ __device__ bool tile(const Operands &p, const CUtensorMap *tmA, const CUtensorMa
     if (p.tmaA) tma_box(sA + st * kMaxTileElems, tmA, &full[st], LAYOUT, TA ? kk0 : i0, TA ? i0 : kk0);
     if (p.tmaB) tma_box(sB + st * kMaxTileElems, tmB, &full[st], LAYOUT, TB ? n0 : kk0, TB ? kk0 : n0);
   };
-  if (tid == 0 && any_tma)
+  if (tid == 0)
     for (int s = 0; s < kStages && s < ktiles; ++s) issue(s);
 
   const int c_lane = g & 3;
@@ -132,6 +144,15 @@ __device__ bool tile(const Operands &p, const CUtensorMap *tmA, const CUtensorMa
   const uint32_t negA = ((p.negmask >> (4 * c_lane + t)) & 1u) << 31;
   const int arow = wm * 8 + (g >> 2);
   const int bcol = wn * WN + g;
+
+  // DMMA blocks (4 quaternion rows x 8 columns) entirely past the edge of C
+  // are skipped, and so are k steps past k: ragged problems pay only for the
+  // DMMA granularity, not for the whole tile (warp-uniform conditions)
+  bool row_live[2], col_live[NC];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) row_live[r] = i0 + wm * 8 + 4 * r < p.m;
+#pragma unroll
+  for (int cc = 0; cc < NC; ++cc) col_live[cc] = n0 + wn * WN + 8 * cc < p.n;
 
   double acc[2][NC][4];
 #pragma unroll
@@ -154,8 +175,7 @@ __device__ bool tile(const Operands &p, const CUtensorMap *tmA, const CUtensorMa
     if (!p.tmaB)
       load_tile_plain<LAYOUT, B_R, B_C>(b_t, p.B, p.b_rows, p.b_cols, p.ldb, p.psB,
                                         TB ? n0 : kk0, TB ? kk0 : n0);
-    bool ok = true;
-    if (any_tma) ok = mbar_wait_bounded(&full[st], par, limit_ns);
+    const bool ok = mbar_wait_bounded(&full[st], par, limit_ns);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicCAS(err_word, 0, QGEMM_ERR_TIMEOUT);
@@ -166,8 +186,9 @@ __device__ bool tile(const Operands &p, const CUtensorMap *tmA, const CUtensorMa
       }
       return false;
     }
+    const int kk_end = static_cast<int>(min(static_cast<int64_t>(kBKQ), p.k - kk0));
 #pragma unroll 4
-    for (int kk = 0; kk < kBKQ; ++kk) {
+    for (int kk = 0; kk < kk_end; ++kk) {
       double a[2][2], b[NC];
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
@@ -183,12 +204,17 @@ __device__ bool tile(const Operands &p, const CUtensorMap *tmA, const CUtensorMa
         b[cc] = b_t[TB ? tile_idx<LAYOUT, B_R, B_C>(j, kk, t) : tile_idx<LAYOUT, B_R, B_C>(kk, j, t)];
       }
 #pragma unroll
-      for (int r = 0; r < 2; ++r)
+      for (int r = 0; r < 2; ++r) {
+        if (!row_live[r]) continue;
 #pragma unroll
-        for (int cc = 0; cc < NC; ++cc) dmma_16x8x4(acc[r][cc], a[r][0], a[r][1], b[cc]);
+        for (int cc = 0; cc < NC; ++cc) {
+          if (!col_live[cc]) continue;
+          dmma_16x8x4(acc[r][cc], a[r][0], a[r][1], b[cc]);
+        }
+      }
     }
     __syncthreads();
-    if (tid == 0 && any_tma && kt + kStages < ktiles) issue(kt + kStages);
+    if (tid == 0 && kt + kStages < ktiles) issue(kt + kStages);
   }
   kb_run += ktiles;
 
@@ -209,7 +235,9 @@ __device__ bool tile(const Operands &p, const CUtensorMap *tmA, const CUtensorMa
       for (int e = 0; e < 4; ++e) {
         const int64_t qi = i0 + arow + 4 * r + 2 * (e >> 1);
         const int64_t qn = n0 + wn * WN + 8 * cc + 2 * t + (e & 1);
-        const bool inb = qi < p.m && qn < p.n;
+        bool inb = qi < p.m && qn < p.n;
+        if (p.tri == 1) inb = inb && qi >= qn;
+        if (p.tri == 2) inb = inb && qi <= qn;
         double P[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) P[j] = __shfl_sync(0xffffffffu, acc[r][cc][e], src_base | (j << 2));
@@ -227,6 +255,7 @@ __device__ bool tile(const Operands &p, const CUtensorMap *tmA, const CUtensorMa
 #pragma unroll
           for (int j = 0; j < 4; ++j) out = fma(lb[j], Cq[j], out);
         }
+        if (p.tri && qi == qn && c_lane != 0) out = 0.0;  // Hermitian diagonal is real
         if (inb) *dst = out;
       }
   return true;

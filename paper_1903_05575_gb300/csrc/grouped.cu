@@ -235,7 +235,42 @@ struct SplitLayout {
 
 int64_t split_kp(int64_t k) { return ((4 * k + split::BK - 1) / split::BK) * split::BK; }
 
-SplitLayout layout_split(const std::vector<GemmDesc> &ds) {
+// Conjugate transpose of an op: (op(X))^H = op'(X).
+int op_conjtrans(int op) {
+  switch (op) {
+    case QGEMM_OP_N: return QGEMM_OP_H;
+    case QGEMM_OP_H: return QGEMM_OP_N;
+    case QGEMM_OP_T: return QGEMM_OP_C;
+    default: return QGEMM_OP_T;
+  }
+}
+
+// (AB)^H = B^H A^H (Sec. 2.2): when it pads less (tile rows are padded to
+// 128, columns to 64), a problem is computed as D = op(B)^H op(A)^H and
+// written back as C = conj(D)^T by the epilogue.
+GemmDesc oriented(const GemmDesc &d, bool *swapped) {
+  const int64_t pad_n = ((d.m + split::BM - 1) / split::BM) * split::BM *
+                        (((d.n + split::BNQ - 1) / split::BNQ) * split::BNQ);
+  const int64_t pad_s = ((d.n + split::BM - 1) / split::BM) * split::BM *
+                        (((d.m + split::BNQ - 1) / split::BNQ) * split::BNQ);
+  *swapped = d.k > 0 && pad_s < pad_n && std::getenv("QGEMM_GROUPED_NO_SWAP") == nullptr;
+  if (!*swapped) return d;
+  GemmDesc t = d;
+  t.m = d.n;
+  t.n = d.m;
+  t.opA = op_conjtrans(d.opB);
+  t.opB = op_conjtrans(d.opA);
+  t.A = d.B;
+  t.B = d.A;
+  return t;
+}
+
+SplitLayout layout_split(const std::vector<GemmDesc> &ds_in) {
+  std::vector<GemmDesc> ds(ds_in.size());
+  for (size_t p = 0; p < ds_in.size(); ++p) {
+    bool sw;
+    ds[p] = oriented(ds_in[p], &sw);
+  }
   SplitLayout L{};
   int64_t tiles = 0, ptiles = 0;
   L.a_off.resize(ds.size());
@@ -300,9 +335,16 @@ int set_split_smem() {
   return QGEMM_SUCCESS;
 }
 
-int prepare_split(const std::vector<GemmDesc> &ds, int layout, unsigned char *ws,
+int prepare_split(const std::vector<GemmDesc> &ds_in, int layout, unsigned char *ws,
                   size_t ws_bytes, cudaStream_t s, qgemm_grouped_plan *plan) {
-  const SplitLayout L = layout_split(ds);
+  const SplitLayout L = layout_split(ds_in);
+  std::vector<GemmDesc> ds(ds_in.size());
+  std::vector<int> swapped(ds_in.size(), 0);
+  for (size_t p = 0; p < ds_in.size(); ++p) {
+    bool sw;
+    ds[p] = oriented(ds_in[p], &sw);
+    swapped[p] = sw ? 1 : 0;
+  }
   if (ws_bytes < L.total) return -6;
   if (L.tiles > 0x7fffffff || L.ptiles > 0x7fffffff) return QGEMM_ERR_UNSUPPORTED;
   int rc = set_split_smem();
@@ -330,6 +372,7 @@ int prepare_split(const std::vector<GemmDesc> &ds, int layout, unsigned char *ws
     q.g.C = static_cast<float *>(d.C);
     q.g.ldc = d.ldc;
     q.g.psC = d.psc;
+    q.g.swap = swapped[p];
     for (int c = 0; c < 4; ++c) {
       q.g.alpha[c] = static_cast<float>(d.alpha[c]);
       q.g.beta[c] = static_cast<float>(d.beta[c]);
@@ -395,6 +438,192 @@ int prepare_split(const std::vector<GemmDesc> &ds, int layout, unsigned char *ws
   return QGEMM_SUCCESS;
 }
 
+// ---- split precision, fused (no operand workspace) ----
+}  // namespace
+
+// 3-D FP32 tensor map of a stored operand for a box of R x CC stored elements
+// (component x row x column interleaved; row x column x plane for planes).
+bool encode_fp32_operand(CUtensorMap *map, const MatView &v, int layout, int R, int CC) {
+  const uintptr_t base = reinterpret_cast<uintptr_t>(v.ptr);
+  if (base % 16 != 0 || v.rows <= 0 || v.cols <= 0) return false;
+  cuuint64_t dims[3], strides[2];
+  cuuint32_t box[3], estr[3] = {1, 1, 1};
+  if (layout == QGEMM_INTERLEAVED) {
+    dims[0] = 4;
+    dims[1] = static_cast<cuuint64_t>(v.rows);
+    dims[2] = static_cast<cuuint64_t>(v.cols);
+    strides[0] = 16;
+    strides[1] = static_cast<cuuint64_t>(v.ld) * 16;
+    box[0] = 4;
+    box[1] = R;
+    box[2] = CC;
+  } else {
+    if (v.ld % 4 != 0 || v.ps % 4 != 0) return false;
+    dims[0] = static_cast<cuuint64_t>(v.rows);
+    dims[1] = static_cast<cuuint64_t>(v.cols);
+    dims[2] = 4;
+    strides[0] = static_cast<cuuint64_t>(v.ld) * 4;
+    strides[1] = static_cast<cuuint64_t>(v.ps) * 4;
+    box[0] = R;
+    box[1] = CC;
+    box[2] = 4;
+  }
+  if (dims[0] >= (1ull << 32) || dims[1] >= (1ull << 32) || dims[2] >= (1ull << 32)) return false;
+  if (strides[0] >= (1ull << 40) || strides[1] >= (1ull << 40)) return false;
+  EncodeTiledFn enc = encode_tiled_fn();
+  if (!enc) return false;
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(v.ptr), dims, strides,
+             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+namespace {
+
+struct FusedLayout {
+  size_t desc_off, tile_off, total;
+  int64_t tiles;
+};
+
+FusedLayout layout_fused(const std::vector<GemmDesc> &ds) {
+  FusedLayout L{};
+  int64_t tiles = 0;
+  for (const GemmDesc &d : ds)
+    if (d.m > 0 && d.n > 0)
+      tiles += ((d.m + split::BM - 1) / split::BM) * ((d.n + split::BNQ - 1) / split::BNQ);
+  L.tiles = tiles;
+  L.desc_off = kHeaderBytes;
+  L.tile_off = align_up(L.desc_off + ds.size() * sizeof(split::FusedProb), 256);
+  L.total = align_up(L.tile_off + static_cast<size_t>(tiles) * sizeof(int4), 256);
+  return L;
+}
+
+// Fills the fused descriptors; false if some operand cannot be read by TMA.
+bool fused_descs(const std::vector<GemmDesc> &ds, int layout, split::FusedProb *hd) {
+  for (size_t p = 0; p < ds.size(); ++p) {
+    const GemmDesc &d = ds[p];
+    if (d.m == 0 || d.n == 0) continue;
+    split::FusedProb &q = hd[p];
+    const bool ta = op_trans(d.opA), tb = op_trans(d.opB);
+    q.o.layout = layout;
+    q.o.ta = ta ? 1 : 0;
+    q.o.tb = tb ? 1 : 0;
+    q.o.conj_a = op_conj(d.opA) ? 0xEu : 0u;
+    q.o.conj_b = op_conj(d.opB) ? 0xEu : 0u;
+    q.g.m = d.m;
+    q.g.n = d.n;
+    q.g.num_kb = static_cast<int>((d.k + split::FKQ - 1) / split::FKQ);
+    q.g.num_mt = static_cast<int>((d.m + split::BM - 1) / split::BM);
+    q.g.num_nt = static_cast<int>((d.n + split::BNQ - 1) / split::BNQ);
+    q.g.layout = layout;
+    q.g.beta_zero = d.beta_zero ? 1 : 0;
+    q.g.c_vec4 = (reinterpret_cast<uintptr_t>(d.C) % 16 == 0) ? 1 : 0;
+    q.g.C = static_cast<float *>(d.C);
+    q.g.ldc = d.ldc;
+    q.g.psC = d.psc;
+    for (int c = 0; c < 4; ++c) {
+      q.g.alpha[c] = static_cast<float>(d.alpha[c]);
+      q.g.beta[c] = static_cast<float>(d.beta[c]);
+    }
+    if (d.k > 0) {
+      if (!encode_fp32_operand(&q.tmA, d.A, layout, ta ? split::FKQ : split::BM,
+                               ta ? split::BM : split::FKQ))
+        return false;
+      if (!encode_fp32_operand(&q.tmB, d.B, layout, tb ? split::BNQ : split::FKQ,
+                               tb ? split::FKQ : split::BNQ))
+        return false;
+    }
+  }
+  return true;
+}
+
+int set_fused_smem() {
+  static bool done[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return QGEMM_ERR_UNSUPPORTED;
+  if (!done[dev]) {
+    if (cudaFuncSetAttribute(split::fused_kernel<GroupedErr, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(split::kFusedSmemBytes)) != cudaSuccess) {
+      cudaGetLastError();
+      return QGEMM_ERR_CUDA;
+    }
+    done[dev] = true;
+  }
+  return QGEMM_SUCCESS;
+}
+
+// Returns QGEMM_ERR_UNSUPPORTED (before touching the workspace) when some
+// operand is not TMA-addressable; the caller then takes the pre-pass path.
+int prepare_fused(const std::vector<GemmDesc> &ds, int layout, unsigned char *ws,
+                  size_t ws_bytes, cudaStream_t s, qgemm_grouped_plan *plan) {
+  const FusedLayout L = layout_fused(ds);
+  if (L.tiles > 0x7fffffff) return QGEMM_ERR_UNSUPPORTED;
+  std::vector<unsigned char> host(L.total - L.desc_off, 0);
+  auto *hd = reinterpret_cast<split::FusedProb *>(host.data());
+  if (!fused_descs(ds, layout, hd)) return QGEMM_ERR_UNSUPPORTED;
+  if (ws_bytes < L.total) return -6;
+  int rc = set_fused_smem();
+  if (rc) return rc;
+  std::vector<int4> tiles;
+  std::vector<int> tile_kb;
+  for (size_t p = 0; p < ds.size(); ++p) {
+    const GemmDesc &d = ds[p];
+    if (d.m == 0 || d.n == 0) continue;
+    for (int a = 0; a < hd[p].g.num_mt; ++a)
+      for (int b = 0; b < hd[p].g.num_nt; ++b) {
+        tiles.push_back(make_int4(static_cast<int>(p), a, b, 0));
+        tile_kb.push_back(hd[p].g.num_kb);
+      }
+  }
+  std::vector<int32_t> order(tiles.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<int32_t>(i);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t a, int32_t b) { return tile_kb[a] > tile_kb[b]; });
+  int4 *ht = reinterpret_cast<int4 *>(host.data() + (L.tile_off - L.desc_off));
+  for (size_t i = 0; i < order.size(); ++i) ht[i] = tiles[order[i]];
+  if (!host.empty() && cudaMemcpyAsync(ws + L.desc_off, host.data(), host.size(),
+                                       cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    cudaGetLastError();
+    return QGEMM_ERR_CUDA;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  plan->workspace_bytes = L.total;
+  plan->tiles = L.tiles;
+  plan->grid = static_cast<int32_t>(std::min<int64_t>(std::max<int64_t>(L.tiles, 1), sms));
+  plan->desc_offset = static_cast<int64_t>(L.desc_off);
+  plan->tile_offset = static_cast<int64_t>(L.tile_off);
+  plan->data_offset = static_cast<int64_t>(L.total);
+  plan->reserved[2] = 1;  // fused
+  return QGEMM_SUCCESS;
+}
+
+int launch_fused(const qgemm_grouped_plan *plan, cudaStream_t s) {
+  unsigned char *ws = static_cast<unsigned char *>(plan->workspace);
+  const auto *probs = reinterpret_cast<const split::FusedProb *>(ws + plan->desc_offset);
+  const auto *tiles = reinterpret_cast<const int4 *>(ws + plan->tile_offset);
+  CUtensorMap none;
+  std::memset(&none, 0, sizeof(none));
+  split::GemmParams g{};
+  split::FusedOps o{};
+  const char *env = std::getenv("QGEMM_SPLIT_CHUNK");
+  const int chunk = (env && std::atoi(env) > 0) ? std::atoi(env) : 2;
+  split::fused_kernel<GroupedErr, true>
+      <<<plan->grid, split::kFusedThreads, split::kFusedSmemBytes, s>>>(
+          none, none, g, o, probs, tiles, static_cast<int>(plan->tiles), chunk, wait_limit_ns());
+  return launch_status();
+}
+
+// The fused path is opt-in (QGEMM_GROUPED_FUSED=1): measured on GB300 its two
+// converter warps limit it below the pre-pass path (config-4 batch 26.7 vs
+// 47.9 TFLOP/s), and more converter warps do not fit the register budget.
+bool fused_enabled() {
+  const char *e = std::getenv("QGEMM_GROUPED_FUSED");
+  return e && e[0] == '1';
+}
+
 int launch_split(const qgemm_grouped_plan *plan, cudaStream_t s) {
   unsigned char *ws = static_cast<unsigned char *>(plan->workspace);
   const auto *probs = reinterpret_cast<const split::SplitProb *>(ws + plan->desc_offset);
@@ -403,7 +632,7 @@ int launch_split(const qgemm_grouped_plan *plan, cudaStream_t s) {
   const int np = static_cast<int>(plan->reserved[1]);
   if (np > 0) {
     grouped_prepass_kernel<<<plan->reserved0, 256, 0, s>>>(probs, ptiles, np);
-    if (cudaGetLastError() != cudaSuccess) return QGEMM_ERR_CUDA;
+    if (int rc_ = launch_status()) return rc_;
   }
   CUtensorMap none;
   std::memset(&none, 0, sizeof(none));
@@ -412,7 +641,7 @@ int launch_split(const qgemm_grouped_plan *plan, cudaStream_t s) {
   const int chunk = (env && std::atoi(env) > 0) ? std::atoi(env) : 2;
   split::gemm_kernel<GroupedErr, true><<<plan->grid, split::kThreads, split::kSmemBytes, s>>>(
       none, none, g, probs, tiles, static_cast<int>(plan->tiles), chunk, wait_limit_ns());
-  return cudaGetLastError() == cudaSuccess ? QGEMM_SUCCESS : QGEMM_ERR_CUDA;
+  return launch_status();
 }
 
 }  // namespace
@@ -438,6 +667,11 @@ size_t qgemm_grouped_workspace_bytes(const qgemm_problem *problems, int64_t coun
   std::vector<GemmDesc> ds;
   if (validate_problems(problems, count, layout, precision, &ds)) return 0;
   if (precision == QGEMM_FP64) return layout_fp64(ds).total;
+  if (fused_enabled()) {
+    std::vector<unsigned char> probe(ds.size() * sizeof(split::FusedProb), 0);
+    if (fused_descs(ds, layout, reinterpret_cast<split::FusedProb *>(probe.data())))
+      return layout_fused(ds).total;
+  }
   return layout_split(ds).total;
 }
 
@@ -457,6 +691,11 @@ int qgemm_grouped_prepare(const qgemm_problem *problems, int64_t count, int layo
     plan->layout = layout;
     plan->precision = precision;
     plan->count = count;
+    if (fused_enabled()) {
+      rc = prepare_fused(ds, layout, static_cast<unsigned char *>(workspace), workspace_bytes,
+                         static_cast<cudaStream_t>(stream), plan);
+      if (rc != QGEMM_ERR_UNSUPPORTED) return rc;
+    }
     return prepare_split(ds, layout, static_cast<unsigned char *>(workspace), workspace_bytes,
                          static_cast<cudaStream_t>(stream), plan);
   }
@@ -534,7 +773,8 @@ int qgemm_grouped_launch(const qgemm_grouped_plan *plan, void *stream) {
   int rc = device_ready();
   if (rc) return rc;
   if (plan->precision == QGEMM_FP32_SPLIT_BF16)
-    return launch_split(plan, static_cast<cudaStream_t>(stream));
+    return plan->reserved[2] == 1 ? launch_fused(plan, static_cast<cudaStream_t>(stream))
+                                  : launch_split(plan, static_cast<cudaStream_t>(stream));
   rc = set_grouped_smem(plan->layout);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -553,7 +793,7 @@ int qgemm_grouped_launch(const qgemm_grouped_plan *plan, void *stream) {
   else
     grouped_fp64_kernel<1><<<plan->grid, fp64::kThreads, fp64::kSmemBytes, s>>>(
         descs, tiles, nt, counter, wait_limit_ns());
-  return cudaGetLastError() == cudaSuccess ? QGEMM_SUCCESS : QGEMM_ERR_CUDA;
+  return launch_status();
 }
 
 int qgemm_batched_grouped(const qgemm_problem *problems, int64_t count, int layout,

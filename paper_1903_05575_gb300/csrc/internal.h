@@ -29,6 +29,7 @@ struct GemmDesc {
   int64_t ldc, psc;
   int layout;
   bool beta_zero;
+  int tri;  // 0: full C; 1: lower triangle only; 2: upper (Hermitian rank-k update)
 };
 
 inline bool op_trans(int op) { return op == QGEMM_OP_T || op == QGEMM_OP_H; }
@@ -41,6 +42,11 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeTiledFn encode_tiled_fn();
 
+// Status of the launches just made: QGEMM_SUCCESS, or QGEMM_ERR_CUDA with the
+// CUDA error recorded for qgemm_last_cuda_error().
+int launch_status();
+int record_cuda_error(cudaError_t e);
+
 // Device wait limit for bounded spins (env QGEMM_WAIT_LIMIT_MS, default 2000).
 uint64_t wait_limit_ns();
 
@@ -50,6 +56,7 @@ int device_ready();
 // Launchers (return QGEMM status codes).
 int launch_fp64_gemm(const GemmDesc &d, cudaStream_t stream);
 int launch_scale(const GemmDesc &d, bool fp64, cudaStream_t stream);
+int launch_herk_scale(const GemmDesc &d, bool fp64, cudaStream_t stream);
 int split_workspace_bytes(const GemmDesc &d, size_t *bytes);
 int launch_split_gemm(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_t stream);
 int noalloc_scratch(void **out);

@@ -74,11 +74,11 @@ __global__ void probe_ffma_kernel(int iters, float seed) {
 
 }  // namespace
 
-int probe_tcgen05_bf16(double seconds, double *tflops, cudaStream_t stream);
+int probe_tcgen05_bf16(int which, double seconds, double *tflops, cudaStream_t stream);
 
 int debug_unsatisfied_wait(uint64_t limit_ns, cudaStream_t stream) {
   unsatisfied_wait_kernel<<<1, 32, 0, stream>>>(limit_ns);
-  return cudaGetLastError() == cudaSuccess ? QGEMM_SUCCESS : QGEMM_ERR_CUDA;
+  return launch_status();
 }
 
 int misc_take_device_error() {
@@ -92,7 +92,7 @@ int misc_take_device_error() {
 }
 
 int probe_peak(int which, double seconds, double *tflops, cudaStream_t stream) {
-  if (which == 3) return probe_tcgen05_bf16(seconds, tflops, stream);
+  if (which >= 3) return probe_tcgen05_bf16(which, seconds, tflops, stream);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -30,29 +30,40 @@ __global__ void __launch_bounds__(256) split_prepass_kernel(const PrepArgs p) {
 }
 
 // ----------------------------------------------------- tcgen05 probe ---
-// Back-to-back M=128, N=256, K=16 BF16 MMAs on a fixed shared-memory tile
-// (contents irrelevant), one CTA per SM: the tensor-pipe throughput of the
-// instruction shape the GEMM uses.
+// Back-to-back M=128, N=PN, K=16 BF16 MMAs on a fixed shared-memory tile,
+// one CTA per SM: the tensor-pipe throughput of one instruction shape.  FILL
+// puts integer values in [-127, 127] in the tile (as the GEMMs see), else
+// zeros (lower power, so higher clocks).
+template <int PN, bool FILL>
 __global__ void __launch_bounds__(128, 1) tc_probe_kernel(int iters, uint64_t limit_ns) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t raw_addr = smem_u32(smem_raw);
   unsigned char *buf = smem_raw + ((1024 - (raw_addr & 1023)) & 1023);
   __shared__ uint64_t bar;
   __shared__ uint32_t tbase;
+  constexpr uint32_t kBBytes = PN * BK * 2;
   const int warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < (kATermBytes + kBTermBytes) / 16; i += blockDim.x)
-    reinterpret_cast<uint4 *>(buf)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = threadIdx.x; i < static_cast<int>((kATermBytes + kBBytes) / 4); i += blockDim.x) {
+    uint32_t w = 0;
+    if (FILL) {
+      const uint32_t h0 = (2u * i + 1u) * 2654435761u, h1 = (2u * i + 2u) * 2654435761u;
+      const float f0 = static_cast<float>(static_cast<int>((h0 >> 16) % 255u) - 127);
+      const float f1 = static_cast<float>(static_cast<int>((h1 >> 16) % 255u) - 127);
+      w = (__float_as_uint(f0) >> 16) | (__float_as_uint(f1) & 0xffff0000u);
+    }
+    reinterpret_cast<uint32_t *>(buf)[i] = w;
+  }
   fence_proxy_async_smem();
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_barrier_init();
   }
-  if (warp == 0) tmem_alloc(&tbase, BN);
+  if (warp == 0) tmem_alloc(&tbase, PN < 32 ? 32 : PN);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   if (warp == 0 && elect_one()) {
-    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    constexpr uint32_t idesc = idesc_bf16(BM, PN);
     const uint32_t sa = smem_u32(buf), sb = sa + kATermBytes;
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
@@ -67,7 +78,7 @@ __global__ void __launch_bounds__(128, 1) tc_probe_kernel(int iters, uint64_t li
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tbase, BN);
+    tmem_dealloc(tbase, PN < 32 ? 32 : PN);
   }
 }
 
@@ -99,6 +110,7 @@ GemmParams gemm_params(const GemmDesc &d, int64_t kp) {
   g.psC = d.psc;
   g.layout = d.layout;
   g.beta_zero = d.beta_zero ? 1 : 0;
+  g.tri = d.tri;
   g.c_vec4 = (reinterpret_cast<uintptr_t>(d.C) % 16 == 0) ? 1 : 0;
   for (int s = 0; s < 4; ++s) {
     g.alpha[s] = static_cast<float>(d.alpha[s]);
@@ -175,12 +187,63 @@ int launch_prepass(bool is_b, const MatView &v, int op, int64_t rows, int64_t kq
     split_prepass_kernel<true><<<grid, 256, 0, stream>>>(a);
   else
     split_prepass_kernel<false><<<grid, 256, 0, stream>>>(a);
-  return cudaGetLastError() == cudaSuccess ? QGEMM_SUCCESS : QGEMM_ERR_CUDA;
+  return launch_status();
+}
+
+}  // namespace
+
+// 3-D FP32 tensor map of a stored operand (shared with the grouped path).
+bool encode_fp32_operand(CUtensorMap *map, const MatView &v, int layout, int R, int CC);
+
+namespace {
+
+// The fused single-problem path (no workspace) is taken when the caller asks
+// for it with QGEMM_SPLIT_FUSED=1 and every operand is TMA-addressable.
+bool want_fused() {
+  const char *e = std::getenv("QGEMM_SPLIT_FUSED");
+  return e && e[0] == '1';
+}
+
+bool fused_maps(const GemmDesc &d, CUtensorMap *tmA, CUtensorMap *tmB) {
+  const bool ta = op_trans(d.opA), tb = op_trans(d.opB);
+  return encode_fp32_operand(tmA, d.A, d.layout, ta ? FKQ : BM, ta ? BM : FKQ) &&
+         encode_fp32_operand(tmB, d.B, d.layout, tb ? BNQ : FKQ, tb ? FKQ : BNQ);
+}
+
+int launch_fused_single(const GemmDesc &d, const CUtensorMap &tmA, const CUtensorMap &tmB,
+                        cudaStream_t stream) {
+  GemmParams g = gemm_params(d, 4 * d.k);
+  g.num_kb = static_cast<int>((d.k + FKQ - 1) / FKQ);
+  FusedOps o{};
+  o.layout = d.layout;
+  o.ta = op_trans(d.opA) ? 1 : 0;
+  o.tb = op_trans(d.opB) ? 1 : 0;
+  o.conj_a = op_conj(d.opA) ? 0xEu : 0u;
+  o.conj_b = op_conj(d.opB) ? 0xEu : 0u;
+  const int64_t tiles = static_cast<int64_t>(g.num_mt) * g.num_nt;
+  if (tiles > 0x7fffffff) return QGEMM_ERR_UNSUPPORTED;
+  int rc = set_smem(fused_kernel<SplitErr, false>, kFusedSmemBytes);
+  if (rc) return rc;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = static_cast<int>(std::min<int64_t>(tiles, sms));
+  fused_kernel<SplitErr, false><<<grid, kFusedThreads, kFusedSmemBytes, stream>>>(
+      tmA, tmB, g, o, nullptr, nullptr, static_cast<int>(tiles), chunk_for(g.num_kb),
+      wait_limit_ns());
+  return launch_status();
 }
 
 }  // namespace
 
 int split_workspace_bytes(const GemmDesc &d, size_t *bytes) {
+  if (want_fused() && d.k > 0 && d.m > 0 && d.n > 0) {
+    CUtensorMap a, b;
+    if (fused_maps(d, &a, &b)) {
+      *bytes = 0;
+      return QGEMM_SUCCESS;
+    }
+  }
   if (d.k == 0 || d.m == 0 || d.n == 0) {
     *bytes = 0;
     return QGEMM_SUCCESS;
@@ -190,6 +253,12 @@ int split_workspace_bytes(const GemmDesc &d, size_t *bytes) {
 }
 
 int launch_split_gemm(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_t stream) {
+  if (want_fused()) {
+    CUtensorMap fa, fb;
+    std::memset(&fa, 0, sizeof(fa));
+    std::memset(&fb, 0, sizeof(fb));
+    if (fused_maps(d, &fa, &fb)) return launch_fused_single(d, fa, fb, stream);
+  }
   const SplitPlan pl = plan_for(d);
   if (ws_bytes < pl.total || ws == nullptr) return QGEMM_ERR_WORKSPACE;
   auto *wa = static_cast<__nv_bfloat16 *>(ws);
@@ -216,15 +285,16 @@ int launch_split_gemm(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_t
   gemm_kernel<SplitErr, false><<<grid, kThreads, kSmemBytes, stream>>>(
       tmA, tmB, g, nullptr, nullptr, static_cast<int>(tiles), chunk_for(g.num_kb),
       wait_limit_ns());
-  return cudaGetLastError() == cudaSuccess ? QGEMM_SUCCESS : QGEMM_ERR_CUDA;
+  return launch_status();
 }
 
-int probe_tcgen05_bf16(double seconds, double *tflops, cudaStream_t stream) {
+template <int PN, bool FILL>
+int probe_tcgen05_shape(double seconds, double *tflops, cudaStream_t stream) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = 1024 + kATermBytes + kBTermBytes;
-  int rc = set_smem(tc_probe_kernel, smem);
+  const size_t smem = 1024 + kATermBytes + PN * BK * 2;
+  int rc = set_smem(tc_probe_kernel<PN, FILL>, smem);
   if (rc) return rc;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -234,7 +304,7 @@ int probe_tcgen05_bf16(double seconds, double *tflops, cudaStream_t stream) {
   rc = QGEMM_SUCCESS;
   for (int round = 0; round < 8; ++round) {
     cudaEventRecord(e0, stream);
-    tc_probe_kernel<<<sms, 128, smem, stream>>>(iters, wait_limit_ns());
+    tc_probe_kernel<PN, FILL><<<sms, 128, smem, stream>>>(iters, wait_limit_ns());
     cudaEventRecord(e1, stream);
     if (cudaEventSynchronize(e1) != cudaSuccess) {
       rc = QGEMM_ERR_CUDA;
@@ -249,10 +319,20 @@ int probe_tcgen05_bf16(double seconds, double *tflops, cudaStream_t stream) {
   }
   if (rc == QGEMM_SUCCESS && cudaGetLastError() != cudaSuccess) rc = QGEMM_ERR_CUDA;
   if (rc == QGEMM_SUCCESS)
-    *tflops = 2.0 * BM * BN * 16 * 2.0 * iters * sms / (ms * 1e-3) / 1e12;
+    *tflops = 2.0 * BM * PN * 16 * 2.0 * iters * sms / (ms * 1e-3) / 1e12;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return rc;
+}
+
+int probe_tcgen05_bf16(int which, double seconds, double *tflops, cudaStream_t stream) {
+  switch (which) {
+    case 3: return probe_tcgen05_shape<256, false>(seconds, tflops, stream);
+    case 4: return probe_tcgen05_shape<256, true>(seconds, tflops, stream);
+    case 5: return probe_tcgen05_shape<128, true>(seconds, tflops, stream);
+    case 6: return probe_tcgen05_shape<64, true>(seconds, tflops, stream);
+    default: return QGEMM_ERR_UNSUPPORTED;
+  }
 }
 
 // ------------------------------------------------ fixed-scratch variant ---

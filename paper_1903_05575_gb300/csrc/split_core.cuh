@@ -253,6 +253,8 @@ struct GemmParams {
   float *C;
   int64_t ldc, psC;
   float alpha[4], beta[4];
+  int tri;                // 0 full; 1 lower (row >= col) only; 2 upper; real diagonal
+  int swap;               // 1: the kernel computed D = (op(A) op(B))^H; store C = conj(D)^T
 };
 
 // Device descriptor of one problem of a grouped batch.
@@ -292,6 +294,13 @@ __device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity, uint6
   }
 }
 
+// True when tile (mt, nt) has no element in the stored triangle of C.
+__device__ __forceinline__ bool tile_skip(const GemmParams &g, int mt, int nt) {
+  if (g.tri == 1) return static_cast<int64_t>(mt) * BM + BM - 1 < static_cast<int64_t>(nt) * BNQ;
+  if (g.tri == 2) return static_cast<int64_t>(nt) * BNQ + BNQ - 1 < static_cast<int64_t>(mt) * BM;
+  return false;
+}
+
 // Tile t -> problem parameters, tensor maps and tile coordinates.
 template <bool GROUPED>
 __device__ __forceinline__ void tile_of(int t, const GemmParams &single, const CUtensorMap *smA,
@@ -325,6 +334,7 @@ __device__ __forceinline__ void tile_of(int t, const GemmParams &single, const C
 __device__ __forceinline__ void epilogue(const GemmParams &g, int64_t i, int64_t nbase,
                                          const float (&acc)[128]) {
   if (i >= g.m) return;
+  if (g.tri == 2 && nbase + 31 < i) return;
   float sa[4][4], sb[4][4];
 #pragma unroll
   for (int c = 0; c < 4; ++c)
@@ -338,11 +348,21 @@ __device__ __forceinline__ void epilogue(const GemmParams &g, int64_t i, int64_t
   for (int q = 0; q < 32; ++q) {
     const int64_t nn = nbase + q;
     if (nn >= g.n) continue;
-    const float P[4] = {acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]};
+    if ((g.tri == 1 && i < nn) || (g.tri == 2 && i > nn)) continue;
+    float P[4] = {acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]};
+    // element (ci, cj) of C; a transposed problem holds (AB)^H: take conj(D)^T
+    int64_t ci = i, cj = nn;
+    if (g.swap) {
+      ci = nn;
+      cj = i;
+      P[1] = -P[1];
+      P[2] = -P[2];
+      P[3] = -P[3];
+    }
     float cin[4] = {0.f, 0.f, 0.f, 0.f};
     float *dst0;
     if (g.layout == QGEMM_INTERLEAVED) {
-      dst0 = g.C + 4 * (i + nn * g.ldc);
+      dst0 = g.C + 4 * (ci + cj * g.ldc);
       if (!g.beta_zero) {
         if (g.c_vec4) {
           const float4 c4 = *reinterpret_cast<const float4 *>(dst0);
@@ -353,7 +373,7 @@ __device__ __forceinline__ void epilogue(const GemmParams &g, int64_t i, int64_t
         }
       }
     } else {
-      dst0 = g.C + i + nn * g.ldc;
+      dst0 = g.C + ci + cj * g.ldc;
       if (!g.beta_zero) {
 #pragma unroll
         for (int s = 0; s < 4; ++s) cin[s] = dst0[s * g.psC];
@@ -371,6 +391,7 @@ __device__ __forceinline__ void epilogue(const GemmParams &g, int64_t i, int64_t
       out[c] = g.beta_zero ? ap
                            : static_cast<float>(static_cast<double>(ap) + static_cast<double>(bc));
     }
+    if (g.tri && i == nn) out[1] = out[2] = out[3] = 0.f;  // Hermitian diagonal is real
     if (g.layout == QGEMM_INTERLEAVED) {
       if (g.c_vec4)
         *reinterpret_cast<float4 *>(dst0) = make_float4(out[0], out[1], out[2], out[3]);
@@ -432,6 +453,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const CUtensorMap *mA, *mB;
         int mt, nt;
         tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt);
+        if (tile_skip(*g, mt, nt)) continue;
         const int nkb = g->num_kb;
         for (int kb = 0; kb < nkb; ++kb, ++s_run) {
           const int st = s_run % STAGES;
@@ -463,6 +485,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const CUtensorMap *mA, *mB;
         int mt, nt;
         tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt);
+        if (tile_skip(*g, mt, nt)) continue;
         const int nkb = g->num_kb;
         for (int kb = 0; kb < nkb && ok; ++c_run) {
           const int b = c_run & 1;
@@ -518,6 +541,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const CUtensorMap *mA, *mB;
       int mt, nt;
       tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt);
+      if (tile_skip(*g, mt, nt)) continue;
       const int nkb = g->num_kb;
       const int nch = (nkb + chunk - 1) / chunk;
       float acc[128];
@@ -527,6 +551,411 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int b = c_run & 1;
         if (!wait_phase(&ctl->accfull[b], (c_run >> 1) & 1, limit_ns, ctl)) {
           set_abort<Err>(ctl);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t base = tmem + lane_base + b * BN + half * 128;
+        // 32 columns per load: the drain warps' register budget is 168 per
+        // thread (10 warps per CTA, three on some SM sub-partitions)
+#pragma unroll
+        for (int piece = 0; piece < 4; ++piece) {
+          float v[32];
+          tmem_ld32(base + piece * 32, v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) acc[piece * 32 + i] += v[i];
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ctl->accempty[b]);
+      }
+      if (!ok) break;
+      epilogue(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane,
+               static_cast<int64_t>(nt) * BNQ + 32 * half, acc);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+}  // namespace split
+}  // namespace qg
+
+namespace qg {
+namespace split {
+
+// --------------------------------------------------------- fused path ---
+// The same product without a workspace: FP32 tiles of op(A) and op(B) come in
+// by TMA in their stored layout (3-D boxes as in the FP64 path, zero fill past
+// the edges), two converter warps split them into the three BF16 terms and
+// write A' and the sign-expanded B' directly into the 64-byte-swizzled
+// K-major layout of the MMA operands, then hand the stage to the MMA warp
+// (generic-proxy writes made visible to the tensor core by
+// fence.proxy.async).  Used where the operand pre-pass would cost more HBM
+// traffic than it saves (many small problems).
+constexpr int FSTAGES = 2;                          // BF16 operand stages
+constexpr int FSTAGING = 3;                         // FP32 staging slots
+constexpr int kConvWarps = 2;
+constexpr int kFusedThreads = kThreads + 32 * kConvWarps;
+constexpr int FKQ = BK / 4;                         // quaternion k per stage (8)
+constexpr uint32_t kStagingA = BM * FKQ * 16;       // 16 KB FP32 op(A) tile
+constexpr uint32_t kStagingB = BNQ * FKQ * 16;      // 8 KB FP32 op(B) tile
+constexpr uint32_t kStagingBytes = kStagingA + kStagingB;
+constexpr size_t kFusedSmemBytes =
+    1024 + FSTAGES * kStageBytes + FSTAGING * kStagingBytes + 256;
+
+// Per-problem parameters of the fused path.
+struct FusedOps {
+  int layout;
+  int ta, tb;          // op(A) / op(B) transposed (T or H)
+  uint32_t conj_a;     // component sign masks (bit s: negate component s)
+  uint32_t conj_b;
+};
+
+struct alignas(128) FusedProb {
+  CUtensorMap tmA;     // FP32 stored A, 3-D box
+  CUtensorMap tmB;     // FP32 stored B, 3-D box
+  FusedOps o;
+  GemmParams g;
+};
+
+struct FusedCtl {
+  uint64_t sfull[FSTAGING];   // FP32 staging landed (TMA)
+  uint64_t sempty[FSTAGING];  // FP32 staging consumed (converters)
+  uint64_t full[FSTAGES];     // BF16 stage written (converters)
+  uint64_t empty[FSTAGES];    // BF16 stage consumed (MMA commit)
+  uint64_t accfull[2];
+  uint64_t accempty[2];
+  uint64_t done;
+  uint32_t tmem_base;
+  int abort;
+};
+
+// Byte offset of element (row, k) (k < 32 bf16) in a K-major tile with
+// 64-byte rows and the 64-byte swizzle (16-byte chunk index XOR bits 1..2 of
+// the row), the layout TMA writes with CU_TENSOR_MAP_SWIZZLE_64B.
+__device__ __forceinline__ uint32_t sw64_offset(int row, int k) {
+  const int chunk = (k >> 3) ^ ((row >> 1) & 3);
+  return static_cast<uint32_t>(row * 64 + chunk * 16 + (k & 7) * 2);
+}
+
+// Index (in floats) of component s of op-tile element (r, kk) in the FP32
+// staging tile.  The TMA box order is the stored order: for the stored
+// element (sr, sc) of a box with R stored rows and CC stored columns,
+// interleaved: s + 4 (sr + R sc);  planes: sr + R (sc + CC s).
+__device__ __forceinline__ int staging_idx(int layout, bool trans, int R_op, int r, int kk,
+                                           int s) {
+  // op-tile is R_op rows x FKQ k; stored tile is (R_op x FKQ) or transposed
+  const int sr = trans ? kk : r, sc = trans ? r : kk;
+  const int R = trans ? FKQ : R_op, CC = trans ? R_op : FKQ;
+  if (layout == QGEMM_INTERLEAVED) return s + 4 * (sr + R * sc);
+  return sr + R * (sc + CC * s);
+}
+
+__device__ __forceinline__ void store_bf16x4(unsigned char *tile, int row, int k0,
+                                             __nv_bfloat16 a, __nv_bfloat16 b,
+                                             __nv_bfloat16 c, __nv_bfloat16 d) {
+  __align__(8) __nv_bfloat16 w[4] = {a, b, c, d};
+  *reinterpret_cast<uint2 *>(tile + sw64_offset(row, k0)) = *reinterpret_cast<const uint2 *>(w);
+}
+
+// Converter: FP32 staging slot -> BF16 stage (A' rows i, B' rows 4n + c).
+__device__ __forceinline__ void convert_stage(const float *stA, const float *stB,
+                                              unsigned char *stage, const FusedOps &o,
+                                              int ctid) {
+  // A': 128 rows x 8 quaternion k; thread handles (row, kk) pairs
+  for (int e = ctid; e < BM * FKQ; e += 32 * kConvWarps) {
+    const int r = e % BM, kk = e / BM;
+    float v[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      v[s] = stA[staging_idx(o.layout, o.ta, BM, r, kk, s)];
+      if ((o.conj_a >> s) & 1u) v[s] = -v[s];
+    }
+    Split3 sp[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) sp[s] = split3(v[s]);
+#pragma unroll
+    for (int t = 0; t < TERMS; ++t)
+      store_bf16x4(stage + t * kATermBytes, r, 4 * kk, sp[0].t[t], sp[1].t[t], sp[2].t[t],
+                   sp[3].t[t]);
+  }
+  // B': 64 quaternion columns x 8 quaternion k -> rows 4n + c
+  unsigned char *sb = stage + kStageA;
+  for (int e = ctid; e < BNQ * FKQ; e += 32 * kConvWarps) {
+    const int n = e % BNQ, kk = e / BNQ;
+    float v[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      // op(B) tile element (kk, n): use the op-row = n convention of staging_idx
+      v[s] = stB[o.tb ? staging_idx(o.layout, false, BNQ, n, kk, s)
+                      : staging_idx(o.layout, true, BNQ, n, kk, s)];
+      if ((o.conj_b >> s) & 1u) v[s] = -v[s];
+    }
+    Split3 sp[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) sp[s] = split3(v[s]);
+#pragma unroll
+    for (int t = 0; t < TERMS; ++t)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        __nv_bfloat16 w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int q = j ^ c;
+          w[j] = basis_sign(j, q) < 0 ? __hneg(sp[q].t[t]) : sp[q].t[t];
+        }
+        store_bf16x4(sb + t * kBTermBytes, 4 * n + c, 4 * kk, w[0], w[1], w[2], w[3]);
+      }
+  }
+}
+
+__device__ __forceinline__ void tma_stage(float *dst, const CUtensorMap *map, uint64_t *bar,
+                                          int layout, int r0, int c0) {
+  if (layout == QGEMM_INTERLEAVED)
+    tma_load_3d(dst, map, bar, 0, r0, c0);
+  else
+    tma_load_3d(dst, map, bar, r0, c0, 0);
+}
+
+template <bool GROUPED>
+__device__ __forceinline__ void fused_tile_of(int t, const GemmParams &single,
+                                              const FusedOps &single_o, const CUtensorMap *smA,
+                                              const CUtensorMap *smB, const FusedProb *probs,
+                                              const int4 *tiles, const GemmParams *&g,
+                                              const FusedOps *&o, const CUtensorMap *&mA,
+                                              const CUtensorMap *&mB, int &mt, int &nt) {
+  if (GROUPED) {
+    const int4 e = tiles[t];
+    const FusedProb *pr = probs + e.x;
+    g = &pr->g;
+    o = &pr->o;
+    mA = &pr->tmA;
+    mB = &pr->tmB;
+    mt = e.y;
+    nt = e.z;
+  } else {
+    g = &single;
+    o = &single_o;
+    mA = smA;
+    mB = smB;
+    const int per_group = kGroupM * single.num_nt;
+    const int first_m = (t / per_group) * kGroupM;
+    const int gsize = min(single.num_mt - first_m, kGroupM);
+    mt = first_m + (t % per_group) % gsize;
+    nt = (t % per_group) / gsize;
+  }
+}
+
+template <class Err>
+__device__ __forceinline__ void fused_abort(FusedCtl *ctl) {
+  atomicCAS(Err::word(), 0, QGEMM_ERR_TIMEOUT);
+  *reinterpret_cast<volatile int *>(&ctl->abort) = 1;
+}
+__device__ __forceinline__ bool fused_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
+                                           FusedCtl *ctl) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*reinterpret_cast<volatile int *>(&ctl->abort) != 0 || globaltimer_ns() - t0 > limit_ns)
+      return false;
+  }
+}
+
+// Warps: 0 TMA (FP32 staging), 1 MMA, 2..9 drain + epilogue, 10..11 convert.
+template <class Err, bool GROUPED>
+__global__ void __launch_bounds__(kFusedThreads, 1)
+    fused_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 const GemmParams single, const FusedOps single_o,
+                 const FusedProb *__restrict__ probs, const int4 *__restrict__ tiles, int ntiles,
+                 int chunk, uint64_t limit_ns) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uint32_t raw_addr = smem_u32(smem_raw);
+  unsigned char *ring = smem_raw + ((1024 - (raw_addr & 1023)) & 1023);
+  float *staging = reinterpret_cast<float *>(ring + FSTAGES * kStageBytes);
+  FusedCtl *ctl = reinterpret_cast<FusedCtl *>(reinterpret_cast<unsigned char *>(staging) +
+                                               FSTAGING * kStagingBytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < FSTAGING; ++s) {
+      mbar_init(&ctl->sfull[s], 1);
+      mbar_init(&ctl->sempty[s], kConvWarps);
+    }
+    for (int s = 0; s < FSTAGES; ++s) {
+      mbar_init(&ctl->full[s], kConvWarps);
+      mbar_init(&ctl->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&ctl->accfull[b], 1);
+      mbar_init(&ctl->accempty[b], kEpiWarps);
+    }
+    mbar_init(&ctl->done, 1);
+    ctl->abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(&ctl->tmem_base, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ctl->tmem_base;
+
+  if (warp == 0) {
+    // ---------------- TMA producer: FP32 tiles ----------------
+    if (elect_one()) {
+      uint32_t s_run = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const GemmParams *g;
+        const FusedOps *o;
+        const CUtensorMap *mA, *mB;
+        int mt, nt;
+        fused_tile_of<GROUPED>(t, single, single_o, &tmA, &tmB, probs, tiles, g, o, mA, mB, mt,
+                               nt);
+        if (tile_skip(*g, mt, nt)) continue;
+        const int nkb = g->num_kb;
+        const int layout = o->layout, ta = o->ta, tb = o->tb;
+        for (int kb = 0; kb < nkb; ++kb, ++s_run) {
+          const int st = s_run % FSTAGING;
+          if (!fused_wait(&ctl->sempty[st], ((s_run / FSTAGING) & 1) ^ 1, limit_ns, ctl)) {
+            fused_abort<Err>(ctl);
+            ok = false;
+            break;
+          }
+          float *sa = staging + st * (kStagingBytes / 4);
+          float *sb = sa + kStagingA / 4;
+          mbar_arrive_expect_tx(&ctl->sfull[st], kStagingBytes);
+          const int k0 = kb * FKQ;
+          tma_stage(sa, mA, &ctl->sfull[st], layout, ta ? k0 : mt * BM, ta ? mt * BM : k0);
+          tma_stage(sb, mB, &ctl->sfull[st], layout, tb ? nt * BNQ : k0, tb ? k0 : nt * BNQ);
+        }
+      }
+      if (!ok) {
+        for (uint32_t q = s_run > FSTAGING ? s_run - FSTAGING : 0; q < s_run; ++q)
+          mbar_wait_bounded(&ctl->sfull[q % FSTAGING], (q / FSTAGING) & 1, limit_ns);
+      }
+    }
+  } else if (warp >= 2 + kEpiWarps) {
+    // ---------------- converters ----------------
+    const int ctid = threadIdx.x - 32 * (2 + kEpiWarps);
+    uint32_t s_run = 0, b_run = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const GemmParams *g;
+      const FusedOps *o;
+      const CUtensorMap *mA, *mB;
+      int mt, nt;
+      fused_tile_of<GROUPED>(t, single, single_o, &tmA, &tmB, probs, tiles, g, o, mA, mB, mt,
+                             nt);
+      if (tile_skip(*g, mt, nt)) continue;
+      const FusedOps ops = *o;
+      const int nkb = g->num_kb;
+      for (int kb = 0; kb < nkb; ++kb, ++s_run, ++b_run) {
+        const int ss = s_run % FSTAGING, bs = b_run % FSTAGES;
+        if (!fused_wait(&ctl->sfull[ss], (s_run / FSTAGING) & 1, limit_ns, ctl) ||
+            !fused_wait(&ctl->empty[bs], ((b_run / FSTAGES) & 1) ^ 1, limit_ns, ctl)) {
+          fused_abort<Err>(ctl);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const float *sa = staging + ss * (kStagingBytes / 4);
+        convert_stage(sa, sa + kStagingA / 4, ring + bs * kStageBytes, ops, ctid);
+        fence_proxy_async_smem();  // the tensor core reads what the threads wrote
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&ctl->sempty[ss]);
+          mbar_arrive(&ctl->full[bs]);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (elect_one()) {
+      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      const uint32_t ring_addr = smem_u32(ring);
+      uint32_t b_run = 0, c_run = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const GemmParams *g;
+        const FusedOps *o;
+        const CUtensorMap *mA, *mB;
+        int mt, nt;
+        fused_tile_of<GROUPED>(t, single, single_o, &tmA, &tmB, probs, tiles, g, o, mA, mB, mt,
+                               nt);
+        if (tile_skip(*g, mt, nt)) continue;
+        const int nkb = g->num_kb;
+        for (int kb = 0; kb < nkb && ok; ++c_run) {
+          const int b = c_run & 1;
+          if (!fused_wait(&ctl->accempty[b], ((c_run >> 1) & 1) ^ 1, limit_ns, ctl)) {
+            fused_abort<Err>(ctl);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d = tmem + b * BN;
+          const int kb_end = min(nkb, kb + chunk);
+          bool first = true;
+          for (; kb < kb_end; ++kb, ++b_run) {
+            const int st = b_run % FSTAGES;
+            if (!fused_wait(&ctl->full[st], (b_run / FSTAGES) & 1, limit_ns, ctl)) {
+              fused_abort<Err>(ctl);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = ring_addr + st * kStageBytes;
+            const uint32_t sb = sa + kStageA;
+#pragma unroll
+            for (int ks = 0; ks < BK / 16; ++ks) {
+#pragma unroll
+              for (int tp = 0; tp < 6; ++tp) {
+                const uint64_t ad = smem_desc_sw64(sa + term_a(tp) * kATermBytes + ks * 32);
+                const uint64_t bd = smem_desc_sw64(sb + term_b(tp) * kBTermBytes + ks * 32);
+                umma_bf16(d, ad, bd, idesc, first ? 0u : 1u);
+                first = false;
+              }
+            }
+            umma_commit(&ctl->empty[st]);
+          }
+          if (!ok) break;
+          umma_commit(&ctl->accfull[b]);
+        }
+      }
+      umma_commit(&ctl->done);
+      mbar_wait_bounded(&ctl->done, 0, limit_ns);
+    }
+  } else {
+    // ---------------- drain + epilogue (8 warps) ----------------
+    const int ew = warp - 2;
+    const int quad = warp & 3;
+    const int half = ew >> 2;
+    const uint32_t lane_base = static_cast<uint32_t>(32 * quad) << 16;
+    uint32_t c_run = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const GemmParams *g;
+      const FusedOps *o;
+      const CUtensorMap *mA, *mB;
+      int mt, nt;
+      fused_tile_of<GROUPED>(t, single, single_o, &tmA, &tmB, probs, tiles, g, o, mA, mB, mt,
+                             nt);
+      if (tile_skip(*g, mt, nt)) continue;
+      const int nkb = g->num_kb;
+      const int nch = (nkb + chunk - 1) / chunk;
+      float acc[128];
+#pragma unroll
+      for (int i = 0; i < 128; ++i) acc[i] = 0.f;
+      for (int ch = 0; ch < nch; ++ch, ++c_run) {
+        const int b = c_run & 1;
+        if (!fused_wait(&ctl->accfull[b], (c_run >> 1) & 1, limit_ns, ctl)) {
+          fused_abort<Err>(ctl);
           ok = false;
           break;
         }

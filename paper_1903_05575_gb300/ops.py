@@ -77,6 +77,26 @@ def qgemm(opA, opB, m, n, k, alpha, A, B, beta, C, layout="interleaved", ws=None
     return C
 
 
+def qherk(uplo, trans, n, k, alpha, A, beta, C, layout="interleaved", ws=None, stream=None):
+    """Hermitian rank-k update on one triangle of C (real alpha, beta):
+    trans N: C <- alpha A A^H + beta C;  trans H: C <- alpha A^H A + beta C."""
+    prec = precision_of(C.dtype)
+    L = _abi.lib()
+    lda, psA, _ = geometry(A, layout)
+    ldc, psC, _ = geometry(C, layout)
+    up, tr = {"L": 0, "U": 1}[uplo], _abi.OP[trans]
+    need = L.qherk_workspace_bytes(up, tr, n, k, _abi.LAYOUT[layout], _abi.PRECISION[prec])
+    if ws is None:
+        ws = workspace(need, C.device)
+    wptr = ws.data_ptr() if ws is not None else None
+    wbytes = ws.numel() * ws.element_size() if ws is not None else 0
+    rc = L.qherk(up, tr, n, k, float(alpha), A.data_ptr(), lda, psA, float(beta), C.data_ptr(),
+                 ldc, psC, _abi.LAYOUT[layout], _abi.PRECISION[prec], wptr, wbytes,
+                 _stream_handle(stream))
+    _abi.check(rc, "qherk")
+    return C
+
+
 def qgemm_backward(X, W, dY, mb, k, n, dX=None, dW=None, accumulate=False,
                    layout="interleaved", ws=None, stream=None):
     """dX = dY W^H and dW = X^H dY for Y = X W (either output may be None)."""

@@ -1,0 +1,182 @@
+"""Square-size sweeps of the quaternion GEMM (the paper measures square
+N x N products, Sec. 5), printing one JSON line per case:
+
+  fp64:  m = n = k in --sizes, every (opA, opB) in --ops, both layouts;
+         effective TFLOP/s (32 m n k / t), fraction of the measured DMMA
+         peak, relative error on sampled entries against the FP64 oracle.
+  split: m = n = k in --split-sizes, inputs N(0,1) and N(0,1) 2^(u_r + v_c)
+         (u, v integers in [-20, 20] per row and column), op N,N; TFLOP/s,
+         error, speedup over the FP64 rate at the same size.
+
+Timing: CUDA events on the launching stream around `reps` calls after
+warm-up; inputs of every case are larger than L2 except the smallest FP64
+sizes, where the call is run `reps` times on the same data (stated in the
+line).  The oracle is only used for the sampled error.
+
+  python -m paper_1903_05575_gb300.sweep [--sizes 1024,2048,4096] [--ops all|NN]
+"""
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+
+def _timed(fn, reps, warm=1):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _sampled_error(opA, opB, n, alpha, beta, A, B, C0, C, layout, count=256, seed=1):
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import qsynth
+    from oracle import oracle as orc
+    g = np.random.default_rng(seed)
+    rows, cols = g.integers(0, n, count), g.integers(0, n, count)
+    ref = orc.qgemm_entries(opA, opB, n, n, n, alpha, A.double().cpu().numpy(),
+                            B.double().cpu().numpy(), beta, C0.double().cpu().numpy(), rows, cols,
+                            layout=layout)
+    got = qsynth.components(C.double().cpu().numpy(), n, layout)[rows, cols]
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
+def fp64_case(n, opA, opB, layout, peak, reps):
+    import torch
+
+    import qsynth
+    from . import ops
+    dev = torch.device("cuda", torch.cuda.current_device())
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(n + 17 * "NTCH".index(opA) + "NTCH".index(opB))
+    shape = (n, n, 4) if layout == "interleaved" else (4, n, n)
+    A = torch.randn(shape, dtype=torch.float64, device=dev, generator=gen)
+    B = torch.randn(shape, dtype=torch.float64, device=dev, generator=gen)
+    C0 = torch.randn(shape, dtype=torch.float64, device=dev, generator=gen)
+    C = C0.clone()
+    alpha, beta = qsynth.unit_quaternion(n + 1), qsynth.unit_quaternion(n + 2)
+    ms = _timed(lambda: ops.qgemm(opA, opB, n, n, n, alpha, A, B, beta, C, layout=layout), reps)
+    C.copy_(C0)
+    ops.qgemm(opA, opB, n, n, n, alpha, A, B, beta, C, layout=layout)
+    torch.cuda.synchronize()
+    err = _sampled_error(opA, opB, n, alpha, beta, A, B, C0, C, layout)
+    tf = 32.0 * n ** 3 / (ms * 1e-3) / 1e12
+    return {"path": "fp64", "n": n, "op": opA + opB, "layout": layout, "ms": ms, "tflops": tf,
+            "frac_of_dmma_peak": tf / peak, "rel_err_sampled": err, "tolerance": 1e-12,
+            "l2": "inputs %.2f GiB" % (3 * n * n * 32 / 2 ** 30)}
+
+
+def split_case(n, kind, fp64_tflops, reps):
+    import torch
+
+    import qsynth
+    from . import ops
+    dev = torch.device("cuda", torch.cuda.current_device())
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(3 * n + (kind == "scaled"))
+    shape = (n, n, 4)
+
+    def scaled(X):
+        if kind != "scaled":
+            return X
+        u = torch.randint(-20, 21, (n,), device=dev, generator=gen).double()
+        v = torch.randint(-20, 21, (n,), device=dev, generator=gen).double()
+        # interleaved (cols, rows, 4): entry (r, c) scaled by 2^(u_r + v_c)
+        return X * torch.pow(2.0, u[None, :, None] + v[:, None, None]).float()
+    A = scaled(torch.randn(shape, dtype=torch.float32, device=dev, generator=gen))
+    B = scaled(torch.randn(shape, dtype=torch.float32, device=dev, generator=gen))
+    C0 = torch.randn(shape, dtype=torch.float32, device=dev, generator=gen)
+    C = C0.clone()
+    alpha, beta = qsynth.unit_quaternion(n + 3), qsynth.unit_quaternion(n + 4)
+    ms = _timed(lambda: ops.qgemm("N", "N", n, n, n, alpha, A, B, beta, C), reps)
+    C.copy_(C0)
+    ops.qgemm("N", "N", n, n, n, alpha, A, B, beta, C)
+    torch.cuda.synchronize()
+    err = _sampled_error("N", "N", n, alpha, beta, A, B, C0, C, "interleaved", count=512)
+    tf = 32.0 * n ** 3 / (ms * 1e-3) / 1e12
+    return {"path": "split_bf16", "n": n, "inputs": kind, "op": "NN", "layout": "interleaved",
+            "ms": ms, "tflops": tf, "issued_bf16_tflops": 6 * tf, "rel_err_sampled": err,
+            "tolerance": 2e-6, "speedup_vs_fp64": tf / fp64_tflops}
+
+
+def complex_comparison(n, reps, qgemm_ms=None):
+    """The paper's experiment (Sec. 5, Fig. 4) on this GPU: the same product
+    through cuBLAS ZGEMM on the 2n x 2n complex representation (Eq. qmat_complex,
+    Tab. hc_mat_flops: twice the real work of the quaternion product) and cuBLAS
+    DGEMM on the real form
+    (4n x 4n) x (4n x n), against this library's FP64 QGEMM.  cuBLAS is only
+    the comparison system here."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(n)
+    Z1 = torch.randn((2 * n, 2 * n), dtype=torch.complex128, device=dev, generator=gen)
+    Z2 = torch.randn((2 * n, 2 * n), dtype=torch.complex128, device=dev, generator=gen)
+    Z3 = torch.empty_like(Z1)
+    zms = _timed(lambda: torch.matmul(Z1, Z2, out=Z3), reps)
+    del Z1, Z2, Z3
+    R1 = torch.randn((4 * n, 4 * n), dtype=torch.float64, device=dev, generator=gen)
+    R2 = torch.randn((4 * n, n), dtype=torch.float64, device=dev, generator=gen)
+    R3 = torch.empty((4 * n, n), dtype=torch.float64, device=dev)
+    dms = _timed(lambda: torch.matmul(R1, R2, out=R3), reps)
+    del R1, R2, R3
+    if qgemm_ms is None:
+        from . import ops
+        A = torch.randn((n, n, 4), dtype=torch.float64, device=dev, generator=gen)
+        B = torch.randn((n, n, 4), dtype=torch.float64, device=dev, generator=gen)
+        C = torch.empty((n, n, 4), dtype=torch.float64, device=dev)
+        one, zero = (1.0, 0, 0, 0), (0.0, 0, 0, 0)
+        qgemm_ms = _timed(lambda: ops.qgemm("N", "N", n, n, n, one, A, B, zero, C), reps)
+    q = 32.0 * n ** 3
+    return {"path": "comparison", "n": n, "qgemm_fp64_ms": qgemm_ms,
+            "zgemm_2n_ms": zms, "dgemm_real_form_ms": dms,
+            "qgemm_tflops": q / (qgemm_ms * 1e-3) / 1e12,
+            "zgemm_tflops_same_product": q / (zms * 1e-3) / 1e12,
+            "dgemm_tflops_same_product": q / (dms * 1e-3) / 1e12,
+            "zgemm_over_qgemm_time": zms / qgemm_ms, "dgemm_over_qgemm_time": dms / qgemm_ms,
+            "note": "rates count 32 n^3 flops (the quaternion product) for all three"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--sizes", default="1024,2048,4096")
+    ap.add_argument("--ops", default="all")
+    ap.add_argument("--layouts", default="interleaved,planes")
+    ap.add_argument("--split-sizes", default="2048,8192")
+    ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--compare", default="", help="sizes for the cuBLAS ZGEMM/DGEMM comparison")
+    a = ap.parse_args()
+    from . import ops
+    peak = ops.probe_peak(0, 0.4)
+    pairs = ([x + y for x in "NTCH" for y in "NTCH"] if a.ops == "all" else a.ops.split(","))
+    fp64_rate = {}
+    for n in [int(x) for x in a.sizes.split(",") if x]:
+        for layout in a.layouts.split(","):
+            for op in pairs:
+                t0 = time.time()
+                rec = fp64_case(n, op[0], op[1], layout, peak, a.reps)
+                rec["wall_s"] = time.time() - t0
+                fp64_rate[n] = rec["tflops"]
+                print(json.dumps(rec), flush=True)
+    for n in [int(x) for x in a.split_sizes.split(",") if x]:
+        base = fp64_rate.get(n, peak)
+        for kind in ("normal", "scaled"):
+            print(json.dumps(split_case(n, kind, base, max(a.reps, 3))), flush=True)
+    for n in [int(x) for x in a.compare.split(",") if x]:
+        print(json.dumps(complex_comparison(n, a.reps)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -189,3 +189,66 @@ def test_config4_split_batch_sampled_and_graph():
     torch.cuda.synchronize()
     worst = check_batch(host, dev, "interleaved", 2e-6, full=False)
     print("config4 split worst sampled rel err %.3e" % worst)
+
+
+@pytest.mark.parametrize("fused", ["1", "0"])
+def test_split_batch_fused_and_prepass_paths(fused, monkeypatch):
+    """The grouped split path with operands converted in shared memory (fused)
+    and through the workspace pre-pass give oracle-equal results."""
+    monkeypatch.setenv("QGEMM_GROUPED_FUSED", fused)
+    g = qsynth.rng(25)
+    specs = []
+    for i in range(24):
+        m, n, k = (int(x) for x in g.integers(1, 300, size=3))
+        specs.append((OPS[i % 4], OPS[(i // 4) % 4], m, n, k))
+    host, dev = make_batch(specs, "interleaved", dtype=np.float32, seed=900)
+    for h in host:
+        for name in ("A", "B", "C"):
+            h[name] = h[name].astype(np.float32).astype(np.float64)
+    b = GroupedBatch(dev)
+    assert int(b.plan.reserved[2]) == (1 if fused == "1" else 0)
+    b.launch()
+    torch.cuda.synchronize()
+    check_batch(host, dev, "interleaved", 2e-6)
+
+
+@pytest.mark.parametrize("layout", qsynth.LAYOUTS)
+def test_split_batch_transposed_orientation(layout):
+    """Wide problems (m << n) are computed as (op(B)^H op(A)^H) and written
+    back conjugate-transposed; every op pair, against the oracle."""
+    specs = [(a, b, 20 + 3 * i, 200 + 5 * i, 30 + i) for i, (a, b) in
+             enumerate([(x, y) for x in OPS for y in OPS])]
+    host, dev = make_batch(specs, layout, dtype=np.float32, seed=1000)
+    for h in host:
+        for name in ("A", "B", "C"):
+            h[name] = h[name].astype(np.float32).astype(np.float64)
+    b = GroupedBatch(dev, layout=layout)
+    b.launch()
+    torch.cuda.synchronize()
+    check_batch(host, dev, layout, 2e-6)
+
+
+def test_fp64_batch_mixing_tma_and_plain_load_problems():
+    """Problems whose operands TMA cannot address (odd leading dimensions in
+    the planes layout: plain loads) interleaved with TMA problems in the same
+    persistent CTAs: ring slots and barrier phases must stay in step."""
+    set_tile_table([3] * 25)
+    try:
+        host, dev = [], []
+        for i in range(40):
+            m, n, k = 40 + i, 36 + 2 * i, 20 + 3 * i
+            pad_a = 1 if i % 2 else 2   # lda = m + 1 (odd when m even) or m + 2
+            layout = "planes"
+            A = qsynth.normal(m, k, 1300 + i, layout, ld=m + pad_a + (m % 2 if i % 2 else 0))
+            B = qsynth.normal(k, n, 1400 + i, layout, ld=k + (1 - k % 2 if i % 2 else k % 2))
+            C = qsynth.normal(m, n, 1500 + i, layout, ld=m + 1)
+            al, be = qsynth.unit_quaternion(i), qsynth.unit_quaternion(i + 77)
+            host.append(dict(opA="N", opB="N", m=m, n=n, k=k, alpha=al, beta=be, A=A, B=B, C=C))
+            dev.append(dict(opA="N", opB="N", m=m, n=n, k=k, alpha=al, beta=be, A=to_dev(A),
+                            B=to_dev(B), C=to_dev(C)))
+        b = GroupedBatch(dev, layout="planes")
+        b.launch()
+        torch.cuda.synchronize()
+        check_batch(host, dev, "planes", 1e-12)
+    finally:
+        set_tile_table(None)

@@ -11,7 +11,7 @@ import torch
 import qsynth
 from oracle import oracle as orc
 from paper_1903_05575_gb300 import _abi, ops
-from tests.gpu_util import gpu_run, make_case, oracle_full, padding, rel_fro
+from tests.gpu_util import gpu_run, make_case, oracle_full, padding, rel_fro, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -119,3 +119,31 @@ def test_sampled_8192(kind):
     err = _sampled(8192, kind, 8200)
     print("8192 %s sampled rel err %.3e" % (kind, err))
     assert err <= TOL
+
+
+@pytest.mark.parametrize("layout", qsynth.LAYOUTS)
+@pytest.mark.parametrize("opA,opB", [("N", "N"), ("T", "H"), ("C", "T"), ("H", "C")])
+def test_fused_single_problem_path(opA, opB, layout, monkeypatch):
+    """The single-problem fused path (no workspace; operands converted in
+    shared memory) on ragged shapes; planes need ld % 4 == 0 for TMA."""
+    monkeypatch.setenv("QGEMM_SPLIT_FUSED", "1")
+    m, n, k = 150, 70, 45
+    A, B, C = make_case(opA, opB, m, n, k, layout, 1200 + OPS.index(opA), dtype=np.float32,
+                        pad=(4 - qsynth.stored_shape(opA, m, k)[0] % 4 if layout == "planes" else 1,
+                             4 - qsynth.stored_shape(opB, k, n)[0] % 4 if layout == "planes" else 1,
+                             2 if layout == "planes" else 3))
+    ref = oracle_full(opA, opB, m, n, k, ALPHA, A, B, BETA, C, layout)
+    dA, dB, dC = (to_dev(X, torch.float32) for X in (A, B, C))
+    lda, psA, _ = ops.geometry(dA, layout)
+    ldb, psB, _ = ops.geometry(dB, layout)
+    ldc, psC, _ = ops.geometry(dC, layout)
+    # the pointer-less query stays conservative; the call itself needs no workspace
+    rc = _abi.lib().qgemm(OPS.index(opA), OPS.index(opB), m, n, k, _abi.q4(ALPHA), dA.data_ptr(),
+                          lda, psA, dB.data_ptr(), ldb, psB, _abi.q4(BETA), dC.data_ptr(), ldc,
+                          psC, qsynth.LAYOUTS.index(layout), 1, None, 0,
+                          torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    got = dC.double().cpu().numpy()
+    assert rel_fro(qsynth.components(got, m, layout), qsynth.components(ref, m, layout)) <= TOL
+    assert np.all(np.isnan(padding(got, m, layout)))
