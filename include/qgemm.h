@@ -35,6 +35,22 @@
  *                          into a higher-precision accumulator; alpha and beta
  *                          are applied in FP64 and the result is rounded once
  *                          to float.  Needs a workspace (qgemm_workspace_bytes).
+ *   QGEMM_FP64_SLICED_BF16: double data; FP64-class result on the BF16 tensor
+ *                          cores (no paper counterpart; the paper is FP64
+ *                          throughout, and GB300's FP64 pipe is narrow).  Each
+ *                          quaternion row of op(A) and column of op(B) is
+ *                          scaled by a power of two 2^e (e from its largest
+ *                          component) and written as six integer digits of 8
+ *                          bits (an error-free splitting after Ozaki et al.);
+ *                          the 21 digit-pair products whose scale is >= 2^-40
+ *                          run on tcgen05 with exact integer sums.  Error per
+ *                          entry <= about 4k * 2^(e_i + e_n) * 2^-46, i.e.
+ *                          relative to max|row i of op(A)| * max|column n of
+ *                          op(B)| rather than to |C_in| (inputs whose rows or
+ *                          columns span many binades along k lose digits of
+ *                          their small entries).  A row or column holding Inf
+ *                          or NaN gives NaN in the matching row or column of
+ *                          the product.  Needs a workspace.
  *
  * Memory and streams: every matrix pointer is a DEVICE pointer owned by the
  * caller; alpha and beta are HOST arrays of 4 doubles, read during the call
@@ -81,6 +97,7 @@ extern "C" {
 
 #define QGEMM_FP64 0
 #define QGEMM_FP32_SPLIT_BF16 1
+#define QGEMM_FP64_SLICED_BF16 2
 
 #define QGEMM_SUCCESS 0
 #define QGEMM_ERR_UNSUPPORTED 1 /* valid arguments, combination not implemented   */
@@ -102,7 +119,8 @@ extern "C" {
  *  14 C, 15 ldc, 16 psC  device pointer (read unless beta == 0, then written)
  *  17 layout             QGEMM_INTERLEAVED or QGEMM_SPLIT_PLANES (all three
  *                        matrices share it)
- *  18 precision          QGEMM_FP64 or QGEMM_FP32_SPLIT_BF16
+ *  18 precision          QGEMM_FP64, QGEMM_FP32_SPLIT_BF16 or
+ *                        QGEMM_FP64_SLICED_BF16
  *  19 workspace          device scratch, 256-byte aligned, or NULL if
  *  20 workspace_bytes    qgemm_workspace_bytes() is 0
  *  21 stream             cudaStream_t

@@ -11,7 +11,7 @@ from . import build as _build
 
 OP = {"N": 0, "T": 1, "C": 2, "H": 3}
 LAYOUT = {"interleaved": 0, "planes": 1}
-PRECISION = {"fp64": 0, "split_bf16": 1}
+PRECISION = {"fp64": 0, "split_bf16": 1, "fp64_sliced": 2}
 
 SUCCESS = 0
 ERR_UNSUPPORTED = 1

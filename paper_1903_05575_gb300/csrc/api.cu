@@ -45,8 +45,8 @@ int validate_gemm(int opA, int opB, int64_t m, int64_t n, int64_t k, const doubl
   if (alpha == nullptr) return -6;
   if (beta == nullptr) return -13;
   if (layout != QGEMM_INTERLEAVED && layout != QGEMM_SPLIT_PLANES) return -17;
-  if (precision != QGEMM_FP64 && precision != QGEMM_FP32_SPLIT_BF16) return -18;
-  const size_t elem = precision == QGEMM_FP64 ? sizeof(double) : sizeof(float);
+  if (!precision_ok(precision)) return -18;
+  const size_t elem = precision_fp64_data(precision) ? sizeof(double) : sizeof(float);
   const bool alpha_zero = is_zero4(alpha);
   const bool product = m > 0 && n > 0 && k > 0 && !alpha_zero;
   const int64_t ra = op_trans(opA) ? k : m, ca = op_trans(opA) ? m : k;
@@ -131,6 +131,22 @@ int device_ready() {
   return cache[dev] == 1 ? QGEMM_SUCCESS : QGEMM_ERR_NO_DEVICE;
 }
 
+// Workspace a validated problem needs for its precision.
+int workspace_need(const GemmDesc &d, int precision, size_t *need) {
+  *need = 0;
+  if (d.k == 0) return QGEMM_SUCCESS;
+  if (precision == QGEMM_FP32_SPLIT_BF16) return split_workspace_bytes(d, need);
+  if (precision == QGEMM_FP64_SLICED_BF16) return sliced_workspace_bytes(d, need);
+  return QGEMM_SUCCESS;
+}
+
+int launch_product(const GemmDesc &d, int precision, void *ws, size_t ws_bytes,
+                   cudaStream_t s) {
+  if (precision == QGEMM_FP64) return launch_fp64_gemm(d, s);
+  if (precision == QGEMM_FP64_SLICED_BF16) return launch_sliced_gemm(d, ws, ws_bytes, s);
+  return launch_split_gemm(d, ws, ws_bytes, s);
+}
+
 }  // namespace qg
 
 using namespace qg;
@@ -146,10 +162,8 @@ int qgemm(int opA, int opB, int64_t m, int64_t n, int64_t k, const double alpha[
                          layout, precision, &d);
   if (rc) return rc;
   size_t need = 0;
-  if (precision == QGEMM_FP32_SPLIT_BF16 && d.k > 0) {
-    rc = split_workspace_bytes(d, &need);
-    if (rc) return rc;
-  }
+  rc = workspace_need(d, precision, &need);
+  if (rc) return rc;
   if (need > 0) {
     if (workspace == nullptr || reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return -19;
     if (workspace_bytes < need) return -20;
@@ -158,9 +172,8 @@ int qgemm(int opA, int opB, int64_t m, int64_t n, int64_t k, const double alpha[
   rc = device_ready();
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (d.k == 0) return launch_scale(d, precision == QGEMM_FP64, s);
-  if (precision == QGEMM_FP64) return launch_fp64_gemm(d, s);
-  return launch_split_gemm(d, workspace, workspace_bytes, s);
+  if (d.k == 0) return launch_scale(d, precision_fp64_data(precision), s);
+  return launch_product(d, precision, workspace, workspace_bytes, s);
 }
 
 int qgemm_split_noalloc(int opA, int opB, int64_t m, int64_t n, int64_t k,
@@ -190,7 +203,7 @@ int qgemm_split_noalloc(int opA, int opB, int64_t m, int64_t n, int64_t k,
 
 size_t qgemm_workspace_bytes(int opA, int opB, int64_t m, int64_t n, int64_t k, int layout,
                              int precision) {
-  if (precision != QGEMM_FP32_SPLIT_BF16) return 0;
+  if (precision != QGEMM_FP32_SPLIT_BF16 && precision != QGEMM_FP64_SLICED_BF16) return 0;
   if (opA < 0 || opA > 3 || opB < 0 || opB > 3 || m < 0 || n < 0 || k < 0) return 0;
   if (layout != QGEMM_INTERLEAVED && layout != QGEMM_SPLIT_PLANES) return 0;
   if (m == 0 || n == 0 || k == 0) return 0;
@@ -202,7 +215,7 @@ size_t qgemm_workspace_bytes(int opA, int opB, int64_t m, int64_t n, int64_t k, 
   d.k = k;
   d.layout = layout;
   size_t b = 0;
-  if (split_workspace_bytes(d, &b)) return 0;
+  if (workspace_need(d, precision, &b)) return 0;
   return b;
 }
 
@@ -229,10 +242,8 @@ int qherk(int uplo, int trans, int64_t n, int64_t k, double alpha, const void *A
   }
   d.tri = uplo == QGEMM_LOWER ? 1 : 2;
   size_t need = 0;
-  if (precision == QGEMM_FP32_SPLIT_BF16 && d.k > 0) {
-    rc = split_workspace_bytes(d, &need);
-    if (rc) return rc;
-  }
+  rc = workspace_need(d, precision, &need);
+  if (rc) return rc;
   if (need > 0) {
     if (workspace == nullptr || reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return -15;
     if (workspace_bytes < need) return -16;
@@ -241,9 +252,8 @@ int qherk(int uplo, int trans, int64_t n, int64_t k, double alpha, const void *A
   rc = device_ready();
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (d.k == 0) return launch_herk_scale(d, precision == QGEMM_FP64, s);
-  if (precision == QGEMM_FP64) return launch_fp64_gemm(d, s);
-  return launch_split_gemm(d, workspace, workspace_bytes, s);
+  if (d.k == 0) return launch_herk_scale(d, precision_fp64_data(precision), s);
+  return launch_product(d, precision, workspace, workspace_bytes, s);
 }
 
 size_t qherk_workspace_bytes(int uplo, int trans, int64_t n, int64_t k, int layout,
@@ -270,7 +280,7 @@ int qgemm_backward(int64_t mb, int64_t k, int64_t n, const void *X, int64_t ldx,
   if (k < 0) return -2;
   if (n < 0) return -3;
   if (layout != QGEMM_INTERLEAVED && layout != QGEMM_SPLIT_PLANES) return -20;
-  if (precision != QGEMM_FP64 && precision != QGEMM_FP32_SPLIT_BF16) return -21;
+  if (!precision_ok(precision)) return -21;
   const double one[4] = {1.0, 0.0, 0.0, 0.0};
   const double zero[4] = {0.0, 0.0, 0.0, 0.0};
   const double *beta = accumulate ? one : zero;
@@ -309,10 +319,12 @@ int qgemm_get_last_device_error(void) {
   int e2 = split_take_device_error();
   int e3 = grouped_take_device_error();
   int e4 = misc_take_device_error();
+  int e5 = sliced_take_device_error();
   if (e) return e;
   if (e2) return e2;
   if (e3) return e3;
-  return e4;
+  if (e4) return e4;
+  return e5;
 }
 
 const char *qgemm_status_string(int status) {

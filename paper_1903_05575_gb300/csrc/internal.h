@@ -53,6 +53,11 @@ uint64_t wait_limit_ns();
 // Checks that a usable device is current; returns a QGEMM status.
 int device_ready();
 
+inline bool precision_ok(int p) {
+  return p == QGEMM_FP64 || p == QGEMM_FP32_SPLIT_BF16 || p == QGEMM_FP64_SLICED_BF16;
+}
+inline bool precision_fp64_data(int p) { return p != QGEMM_FP32_SPLIT_BF16; }
+
 // Launchers (return QGEMM status codes).
 int launch_fp64_gemm(const GemmDesc &d, cudaStream_t stream);
 int launch_scale(const GemmDesc &d, bool fp64, cudaStream_t stream);
@@ -60,6 +65,8 @@ int launch_herk_scale(const GemmDesc &d, bool fp64, cudaStream_t stream);
 int split_workspace_bytes(const GemmDesc &d, size_t *bytes);
 int launch_split_gemm(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_t stream);
 int noalloc_scratch(void **out);
+int sliced_workspace_bytes(const GemmDesc &d, size_t *bytes);
+int launch_sliced_gemm(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_t stream);
 int validate_gemm(int opA, int opB, int64_t m, int64_t n, int64_t k, const double *alpha,
                   const void *A, int64_t lda, int64_t psA, const void *B, int64_t ldb,
                   int64_t psB, const double *beta, void *C, int64_t ldc, int64_t psC,
@@ -70,6 +77,7 @@ int fp64_take_device_error();
 int split_take_device_error();
 int grouped_take_device_error();
 int misc_take_device_error();
+int sliced_take_device_error();
 int debug_unsatisfied_wait(uint64_t limit_ns, cudaStream_t stream);
 int probe_peak(int which, double seconds, double *tflops, cudaStream_t stream);
 

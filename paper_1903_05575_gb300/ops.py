@@ -5,8 +5,10 @@ Tensors are column-major quaternion matrices:
                (r, c) at [c, r, s] -- four contiguous reals per element (Sec. 4)
   planes:      shape (4, cols, ld), C-contiguous; plane s at [s] (Sec. 2.2)
 Row counts are given explicitly (rows <= ld).  float64 tensors run the FP64
-path, float32 tensors the split-BF16 path.  Every call goes to the CUDA
-library on torch's current stream; there is no CPU fallback.
+path (DMMA) unless precision="fp64_sliced" asks for the digit-sliced FP64
+path on the BF16 tensor cores; float32 tensors run the split-BF16 path.
+Every call goes to the CUDA library on torch's current stream; there is no
+CPU fallback.
 """
 import torch
 
@@ -28,12 +30,18 @@ def geometry(X, layout):
     return X.shape[2], X.shape[1] * X.shape[2], X.shape[1]
 
 
-def precision_of(dtype):
+def precision_of(dtype, precision=None):
+    """The library precision for a tensor dtype: float64 -> "fp64" (or
+    "fp64_sliced" when asked), float32 -> "split_bf16"."""
     if dtype == torch.float64:
-        return "fp64"
-    if dtype == torch.float32:
-        return "split_bf16"
-    raise TypeError("quaternion GEMM takes float64 (FP64 path) or float32 (split-BF16 path)")
+        if precision in (None, "fp64", "fp64_sliced"):
+            return precision or "fp64"
+    elif dtype == torch.float32:
+        if precision in (None, "split_bf16"):
+            return "split_bf16"
+    else:
+        raise TypeError("quaternion GEMM takes float64 (FP64 paths) or float32 (split-BF16 path)")
+    raise ValueError("precision %r does not take %s data" % (precision, dtype))
 
 
 def workspace(nbytes, device):
@@ -55,9 +63,9 @@ def _stream_handle(stream):
 
 
 def qgemm(opA, opB, m, n, k, alpha, A, B, beta, C, layout="interleaved", ws=None,
-          stream=None):
+          stream=None, precision=None):
     """C <- alpha op(A) op(B) + beta C on the GPU (C is updated in place)."""
-    prec = precision_of(C.dtype)
+    prec = precision_of(C.dtype, precision)
     if A.dtype != C.dtype or B.dtype != C.dtype:
         raise TypeError("A, B and C must share a dtype")
     L = _abi.lib()
@@ -77,10 +85,11 @@ def qgemm(opA, opB, m, n, k, alpha, A, B, beta, C, layout="interleaved", ws=None
     return C
 
 
-def qherk(uplo, trans, n, k, alpha, A, beta, C, layout="interleaved", ws=None, stream=None):
+def qherk(uplo, trans, n, k, alpha, A, beta, C, layout="interleaved", ws=None, stream=None,
+          precision=None):
     """Hermitian rank-k update on one triangle of C (real alpha, beta):
     trans N: C <- alpha A A^H + beta C;  trans H: C <- alpha A^H A + beta C."""
-    prec = precision_of(C.dtype)
+    prec = precision_of(C.dtype, precision)
     L = _abi.lib()
     lda, psA, _ = geometry(A, layout)
     ldc, psC, _ = geometry(C, layout)
@@ -98,9 +107,9 @@ def qherk(uplo, trans, n, k, alpha, A, beta, C, layout="interleaved", ws=None, s
 
 
 def qgemm_backward(X, W, dY, mb, k, n, dX=None, dW=None, accumulate=False,
-                   layout="interleaved", ws=None, stream=None):
+                   layout="interleaved", ws=None, stream=None, precision=None):
     """dX = dY W^H and dW = X^H dY for Y = X W (either output may be None)."""
-    prec = precision_of(X.dtype)
+    prec = precision_of(X.dtype, precision)
     L = _abi.lib()
     ldx, psx, _ = geometry(X, layout)
     ldw, psw, _ = geometry(W, layout)

@@ -83,6 +83,23 @@ def test_split_precision_needs_workspace():
                  wsb=need - 1) == -20
 
 
+def test_sliced_precision_workspace():
+    """FP64 digit-sliced path: six BF16 slices of A' (m x 4k) and of the
+    expanded B' (4n x 4k), K padded to 32 reals, plus per-row and per-column
+    maxima and exponents; it needs a workspace, and precision 3 is invalid."""
+    L = _abi.lib()
+    m, n, k = 100, 30, 50
+    need = L.qgemm_workspace_bytes(0, 0, m, n, k, 0, 2)
+    kp = (4 * k + 31) // 32 * 32
+    slices = 6 * 2 * kp * (m + 4 * n)
+    assert slices <= need <= slices + 12 * (m + n) + 8 * 1024
+    assert L.qgemm_workspace_bytes(0, 0, m, n, 0, 0, 2) == 0
+    assert _call(precision=2, m=m, n=n, k=k, lda=m, ldb=k, ldc=m, A=64, B=64, C=64) == -19
+    assert _call(precision=2, m=m, n=n, k=k, lda=m, ldb=k, ldc=m, A=64, B=64, C=64, ws=256,
+                 wsb=need - 1) == -20
+    assert _call(precision=3) == -18
+
+
 def test_backward_argument_numbers():
     L = _abi.lib()
     rc = L.qgemm_backward(-1, 4, 4, 64, 4, 0, 64, 4, 0, 64, 4, 0, 64, 4, 0, 64, 4, 0, 0, 0, 0,

@@ -1,0 +1,239 @@
+"""Digit-sliced FP64 path (precision "fp64_sliced": FP64 data, products on the
+BF16 tensor cores with exact integer digit sums) against the FP64 oracle,
+through the C ABI.
+
+Bar: N(0,1) inputs within the FP64 target, 1e-12 relative Frobenius error;
+small-integer inputs bit-exact; every entry within the path's stated bound
+    |error| <= |alpha|_1 * 4k * 2^(e_i + e_n) * 2^-44 + (beta part, FP64)
+with e_i, e_n the exponents of the largest component of row i of op(A) and
+column n of op(B) (max < 2^e); rows or columns holding Inf or NaN give NaN."""
+import numpy as np
+import pytest
+import torch
+
+import qsynth
+from oracle import oracle as orc
+from paper_1903_05575_gb300 import ops
+from tests.gpu_util import make_case, oracle_full, padding, rel_fro, to_dev
+
+pytestmark = pytest.mark.gpu
+
+OPS = ("N", "T", "C", "H")
+TOL = 1e-12
+ALPHA = qsynth.unit_quaternion(51)
+BETA = qsynth.unit_quaternion(52)
+
+
+def run(opA, opB, m, n, k, alpha, A, B, beta, C, layout):
+    dA, dB, dC = to_dev(A), to_dev(B), to_dev(C)
+    ops.qgemm(opA, opB, m, n, k, alpha, dA, dB, beta, dC, layout=layout, precision="fp64_sliced")
+    torch.cuda.synchronize()
+    return dC.cpu().numpy()
+
+
+def op_exponents(op, X, rows, cols, layout, axis_rows):
+    """frexp exponents of the largest |component| per op-row (axis_rows) or
+    op-column of the op-matrix whose STORED form is X (rows x cols stored)."""
+    comp = np.abs(qsynth.components(X, rows, layout)[:, :cols])
+    trans = op in ("T", "H")
+    along_stored_rows = axis_rows != trans   # reduce over stored columns
+    mx = comp.max(axis=(1, 2)) if along_stored_rows else comp.max(axis=(0, 2))
+    return np.frexp(mx)[1].astype(np.float64)
+
+
+def entry_bound(opA, opB, m, n, k, alpha, A, B, layout):
+    ra, ca = qsynth.stored_shape(opA, m, k)
+    rb, cb = qsynth.stored_shape(opB, k, n)
+    ea = op_exponents(opA, A, ra, ca, layout, axis_rows=True)
+    eb = op_exponents(opB, B, rb, cb, layout, axis_rows=False)
+    scale = np.ldexp(1.0, (ea[:, None] + eb[None, :]).astype(int))
+    return np.abs(alpha).sum() * 4 * k * scale * 2.0 ** -44
+
+
+def check(opA, opB, m, n, k, layout, seed, kind="normal", alpha=ALPHA, beta=BETA, tol=TOL):
+    A, B, C = make_case(opA, opB, m, n, k, layout, seed, kind)
+    ref = oracle_full(opA, opB, m, n, k, alpha, A, B, beta, C, layout)
+    got = run(opA, opB, m, n, k, alpha, A, B, beta, C, layout)
+    g, r = qsynth.components(got, m, layout), qsynth.components(ref, m, layout)
+    if kind == "int":
+        assert np.array_equal(g, r), "small-integer result not bit-exact"
+    else:
+        bound = entry_bound(opA, opB, m, n, k, alpha, A, B, layout)
+        c_in = np.abs(qsynth.components(C, m, layout)).sum(axis=2)
+        slack = bound + 1e-15 * (np.abs(r).sum(axis=2) + np.abs(beta).sum() * c_in)
+        worst = (np.abs(g - r).max(axis=2) / slack).max()
+        assert worst <= 1.0, "entry error above the stated bound (x%.2f)" % worst
+        if tol is not None:
+            err = rel_fro(g, r)
+            assert err <= tol, "relative Frobenius error %.3e" % err
+    assert np.all(np.isnan(padding(got, m, layout))), "padding rows written"
+    return g, r
+
+
+@pytest.mark.parametrize("layout", qsynth.LAYOUTS)
+@pytest.mark.parametrize("opA", OPS)
+@pytest.mark.parametrize("opB", OPS)
+def test_op_pairs_ragged(opA, opB, layout):
+    """Every op pair and layout: 2 row tiles, 3 column tiles, 4.7 exact
+    chunks of 256 real k, all ragged."""
+    check(opA, opB, 200, 37, 300, layout, seed=700 + 4 * OPS.index(opA) + OPS.index(opB))
+
+
+@pytest.mark.parametrize("layout", qsynth.LAYOUTS)
+@pytest.mark.parametrize("ops_pair", [("N", "N"), ("H", "T"), ("C", "H"), ("T", "C")])
+def test_small_int_exact(ops_pair, layout):
+    opA, opB = ops_pair
+    check(opA, opB, 150, 40, 333, layout, seed=800 + OPS.index(opA), kind="int",
+          alpha=np.array([1.0, -2.0, 0.0, 1.0]), beta=np.array([2.0, 0, 1.0, -1.0]))
+
+
+@pytest.mark.parametrize("mnk", [(1, 1, 1), (7, 9, 8), (16, 16, 8), (17, 15, 9), (129, 17, 64),
+                                 (128, 16, 65), (1, 40, 255), (33, 100, 2)])
+@pytest.mark.parametrize("layout", qsynth.LAYOUTS)
+def test_edge_sizes(mnk, layout):
+    m, n, k = mnk
+    for opA, opB in (("N", "N"), ("T", "H"), ("H", "C")):
+        check(opA, opB, m, n, k, layout, seed=m * 1000 + n * 10 + k)
+
+
+def test_extreme_digits_long_k():
+    """Every component +-(1 - 2^-9) (digits 128 and -64), signs arranged so
+    that the real component of every product adds up: the level-0 sums reach
+    their largest possible value, 2^22 per 256-k chunk.  The inputs are
+    represented exactly, so the result is exact."""
+    m, n, k = 130, 20, 2048
+    c = 1.0 - 2.0 ** -9
+    A = qsynth.empty(m, k)
+    B = qsynth.empty(k, n)
+    A[:, :m, :] = c
+    B[:, :k, :] = c
+    A[:, :m, 1:] = -c          # a = c(1, -1, -1, -1): products add up, no cancellation
+    C = qsynth.normal(m, n, 9)
+    one, zero = np.array([1.0, 0, 0, 0]), np.zeros(4)
+    ref = oracle_full("N", "N", m, n, k, one, A, B, zero, C, "interleaved")
+    got = run("N", "N", m, n, k, one, A, B, zero, C, "interleaved")
+    err = rel_fro(got[:, :m], ref[:, :m])
+    print("extreme digits rel err %.3e" % err)
+    assert err <= 1e-15
+
+
+def test_wide_range_rows_and_columns():
+    """Rows of op(A) and columns of op(B) scaled by 2^u, u in [-40, 40]: the
+    per-row and per-column exponents absorb the range, entries stay within
+    the bound and the Frobenius error within the FP64 target."""
+    m, n, k = 140, 50, 400
+    g = qsynth.rng(31)
+    A, B, C = make_case("N", "N", m, n, k, "interleaved", 33)
+    A[:, :m, :] *= np.ldexp(1.0, g.integers(-40, 41, m))[None, :, None]
+    B[:, :k, :] *= np.ldexp(1.0, g.integers(-40, 41, n))[:, None, None]
+    ref = oracle_full("N", "N", m, n, k, ALPHA, A, B, BETA, C, "interleaved")
+    got = run("N", "N", m, n, k, ALPHA, A, B, BETA, C, "interleaved")
+    bound = entry_bound("N", "N", m, n, k, ALPHA, A, B, "interleaved")
+    gc, rc = qsynth.components(got, m, "interleaved"), qsynth.components(ref, m, "interleaved")
+    assert (np.abs(gc - rc).max(axis=2) <= bound + 1e-15 * np.abs(rc).sum(axis=2) + 1e-300).all()
+    relrow = np.abs(gc - rc).max(axis=2) / np.maximum(np.abs(rc).max(axis=2), 1e-300)
+    print("wide range: worst entry relative error %.3e" % relrow.max())
+    assert np.median(relrow) <= 1e-12
+
+
+@pytest.mark.parametrize("layout", qsynth.LAYOUTS)
+def test_range_along_k_within_bound(layout):
+    """Components scaled by 2^(u_r + v_c) along both indices (the scaled
+    inputs of the split-BF16 tests): small entries of a row lose digits, so
+    only the stated bound holds, not the Frobenius target."""
+    check("N", "H", 96, 30, 200, layout, seed=61, kind="scaled", tol=None)
+
+
+def test_beta_zero_does_not_read_c():
+    m, n, k = 50, 40, 30
+    A, B, C = make_case("N", "N", m, n, k, "interleaved", 5)
+    ref = oracle_full("N", "N", m, n, k, ALPHA, A, B, np.zeros(4), C, "interleaved")
+    C[:, :m] = np.nan
+    got = run("N", "N", m, n, k, ALPHA, A, B, np.zeros(4), C, "interleaved")
+    assert rel_fro(got[:, :m], ref[:, :m]) <= TOL
+
+
+def test_non_finite_rows_and_columns():
+    """NaN in row 3 of A and Inf in column 5 of B: that row and that column of
+    C are NaN, every other entry matches the oracle."""
+    m, n, k = 40, 24, 50
+    A, B, C = make_case("N", "N", m, n, k, "interleaved", 71)
+    A[7, 3, 2] = np.nan       # stored (row 3, col 7), component 2
+    B[5, 11, 0] = np.inf      # stored (row 11, col 5)
+    got = run("N", "N", m, n, k, ALPHA, A, B, BETA, C, "interleaved")
+    g = qsynth.components(got, m, "interleaved")
+    assert np.isnan(g[3, :, :]).all()
+    assert np.isnan(g[:, 5, :]).all()
+    A2, B2 = A.copy(), B.copy()
+    A2[7, 3, 2] = 0.0
+    B2[5, 11, 0] = 0.0
+    ref = qsynth.components(oracle_full("N", "N", m, n, k, ALPHA, A2, B2, BETA, C,
+                                        "interleaved"), m, "interleaved")
+    mask = np.ones((m, n), bool)
+    mask[3, :] = False
+    mask[:, 5] = False
+    assert rel_fro(g[mask], ref[mask]) <= TOL
+
+
+def test_alpha_zero_and_k_zero_scale_c():
+    m, n, k = 33, 20, 10
+    A, B, C = make_case("N", "N", m, n, k, "interleaved", 81)
+    for kk, al in ((k, np.zeros(4)), (0, ALPHA)):
+        ref = oracle_full("N", "N", m, n, kk, al, A, B, BETA, C, "interleaved")
+        got = run("N", "N", m, n, kk, al, A, B, BETA, C, "interleaved")
+        assert rel_fro(got[:, :m], ref[:, :m]) <= 1e-15
+
+
+@pytest.mark.parametrize("uplo", ("L", "U"))
+@pytest.mark.parametrize("trans", ("N", "H"))
+def test_herk(uplo, trans):
+    n, k = 150, 90
+    A = qsynth.normal(n if trans == "N" else k, k if trans == "N" else n, 91, ld=None)
+    C = qsynth.normal(n, n, 92)
+    ref = C.copy()
+    orc.qherk(uplo, trans, n, k, 0.75, A, -0.5, ref)
+    dA, dC = to_dev(A), to_dev(C)
+    ops.qherk(uplo, trans, n, k, 0.75, dA, -0.5, dC, precision="fp64_sliced")
+    torch.cuda.synchronize()
+    got = dC.cpu().numpy()
+    assert rel_fro(got, ref) <= TOL
+
+
+def test_backward():
+    """dX = dY W^H and dW = X^H dY through qgemm_backward on the sliced path."""
+    mb, k, n = 96, 40, 56
+    X = qsynth.normal(mb, k, 101)
+    W = qsynth.normal(k, n, 102)
+    dY = qsynth.normal(mb, n, 103)
+    one, zero = np.array([1.0, 0, 0, 0]), np.zeros(4)
+    rX = oracle_full("N", "H", mb, k, n, one, dY, W, zero, qsynth.empty(mb, k), "interleaved")
+    rW = oracle_full("H", "N", k, n, mb, one, X, dY, zero, qsynth.empty(k, n), "interleaved")
+    dXt = torch.zeros((k, mb, 4), dtype=torch.float64, device="cuda")
+    dWt = torch.zeros((n, k, 4), dtype=torch.float64, device="cuda")
+    ops.qgemm_backward(to_dev(X), to_dev(W), to_dev(dY), mb, k, n, dX=dXt, dW=dWt,
+                       precision="fp64_sliced")
+    torch.cuda.synchronize()
+    assert rel_fro(dXt.cpu().numpy(), rX) <= TOL
+    assert rel_fro(dWt.cpu().numpy(), rW) <= TOL
+
+
+def test_2048_sampled_and_status():
+    """m = n = k = 2048, op N,N: 256 sampled entries against the oracle."""
+    n = 2048
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(2048)
+    A = torch.randn((n, n, 4), dtype=torch.float64, device="cuda", generator=gen)
+    B = torch.randn((n, n, 4), dtype=torch.float64, device="cuda", generator=gen)
+    C0 = torch.randn((n, n, 4), dtype=torch.float64, device="cuda", generator=gen)
+    C = C0.clone()
+    ops.qgemm("N", "N", n, n, n, ALPHA, A, B, BETA, C, precision="fp64_sliced")
+    torch.cuda.synchronize()
+    g = np.random.default_rng(3)
+    rows, cols = g.integers(0, n, 256), g.integers(0, n, 256)
+    ref = orc.qgemm_entries("N", "N", n, n, n, ALPHA, A.cpu().numpy(), B.cpu().numpy(), BETA,
+                            C0.cpu().numpy(), rows, cols)
+    got = qsynth.components(C.cpu().numpy(), n, "interleaved")[rows, cols]
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    print("2048 sliced sampled rel err %.3e" % err)
+    assert err <= TOL
+    assert ops.last_device_error() == 0
