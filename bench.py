@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-split", action="store_true")
     p.add_argument("--split-size", type=int, default=8192)
+    p.add_argument("--no-sliced", action="store_true")
+    p.add_argument("--sliced-size", type=int, default=0, help="default: --size")
     p.add_argument("--no-grouped", action="store_true")
     p.add_argument("--grouped-count", type=int, default=4096)
     return p.parse_args()
@@ -294,6 +296,83 @@ def split_section(n, fp64_tflops, steps=5):
             "rel_err_sampled": err, "tolerance": 2e-6,
             "speedup_vs_fp64_path": eff / fp64_tflops,
             "kernels_per_call": 3, "workspace_bytes": need, "clocks": clk.summary()}
+
+
+# ---------------------------------------------------- sliced section ---
+def sliced_section(n, fp64_tflops, steps=5):
+    """The digit-sliced FP64 path (FP64 data, 21 BF16 digit-slice products
+    on tcgen05 with exact integer sums) on the benchmark's workload shape:
+    m = n = k = n, op N,N, interleaved, components iid N(0,1), unit-quaternion
+    alpha and beta; effective and issued TFLOP/s, sampled error against the
+    FP64 oracle, speedup over the DMMA path's measured rate."""
+    import json as _json
+    import numpy as np
+    import torch
+
+    import qsynth
+    from paper_1903_05575_gb300 import _abi
+    dev = torch.device("cuda", torch.cuda.current_device())
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2303)
+    shape = (n, n, 4)
+    A = torch.randn(shape, dtype=torch.float64, device=dev, generator=gen)
+    B = torch.randn(shape, dtype=torch.float64, device=dev, generator=gen)
+    C0 = torch.randn(shape, dtype=torch.float64, device=dev, generator=gen)
+    C = C0.clone()
+    alpha, beta = qsynth.unit_quaternion(2304), qsynth.unit_quaternion(2305)
+    L = _abi.lib()
+    need = L.qgemm_workspace_bytes(0, 0, n, n, n, 0, 2)
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    al, be = _abi.q4(alpha), _abi.q4(beta)
+    stream = torch.cuda.current_stream()
+
+    def step(Cout):
+        rc = L.qgemm(0, 0, n, n, n, al, A.data_ptr(), n, 0, B.data_ptr(), n, 0, be,
+                     Cout.data_ptr(), n, 0, 0, 2, ws.data_ptr(), need, stream.cuda_stream)
+        if rc != 0:
+            raise _abi.QgemmError(rc)
+
+    for _ in range(3):
+        step(C)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0.record(stream)
+        for _ in range(steps):
+            step(C)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    eff = 32.0 * n ** 3 / (ms * 1e-3) / 1e12
+    C.copy_(C0)
+    step(C)
+    torch.cuda.synchronize()
+    from oracle import oracle as orc
+    g = np.random.default_rng(10)
+    rows, cols = g.integers(0, n, 512), g.integers(0, n, 512)
+    ref = orc.qgemm_entries("N", "N", n, n, n, alpha, A.cpu().numpy(), B.cpu().numpy(), beta,
+                            C0.cpu().numpy(), rows, cols)
+    got = qsynth.components(C.cpu().numpy(), n, "interleaved")[rows, cols]
+    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    peaks = {}
+    try:
+        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    return {"config": "fp64 qgemm, digit-sliced on BF16 tensor cores, m=n=k=%d op=NN "
+                      "interleaved N(0,1); 6 digit slices per operand, 21 slice products"
+                      % n,
+            "value": eff, "unit": "TFLOP/s", "ms_per_call": ms,
+            "issued_bf16_tflops": 21.0 * eff,
+            "frac_of_bf16_peak_issued": 21.0 * eff / bf16_peak,
+            "bf16_peak": bf16_peak,
+            "bf16_peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)"
+                                if "bf16_tflops" in peaks else "fallback 1900",
+            "rel_err_sampled": err, "tolerance": 1e-12,
+            "speedup_vs_dmma_path": eff / fp64_tflops,
+            "kernels_per_call": 5, "memsets_per_call": 1, "workspace_bytes": need,
+            "clocks": clk.summary()}
 
 
 # --------------------------------------------------- grouped section ---
@@ -570,6 +649,10 @@ def run_ours(args):
     if not args.no_split:
         split = split_section(args.split_size, achieved)
 
+    sliced = None
+    if not args.no_sliced:
+        sliced = sliced_section(args.sliced_size or n, achieved)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_baseline(n, layout=layout)
@@ -593,6 +676,7 @@ def run_ours(args):
         "gpu_launches": args.steps,
         "cpu_baseline": cpu,
         "split_bf16": split,
+        "fp64_sliced_bf16": sliced,
         "grouped_fp64": grouped,
         "grouped_split_bf16": grouped_split,
     }

@@ -44,7 +44,8 @@
  *                          bits (an error-free splitting after Ozaki et al.);
  *                          the 21 digit-pair products whose scale is >= 2^-40
  *                          run on tcgen05 with exact integer sums.  Error per
- *                          entry <= about 4k * 2^(e_i + e_n) * 2^-46, i.e.
+ *                          entry of op(A) op(B) <= 4k * 2^(e_i + e_n) * 2^-44,
+ *                          i.e.
  *                          relative to max|row i of op(A)| * max|column n of
  *                          op(B)| rather than to |C_in| (inputs whose rows or
  *                          columns span many binades along k lose digits of

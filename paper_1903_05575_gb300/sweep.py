@@ -7,6 +7,8 @@ N x N products, Sec. 5), printing one JSON line per case:
   split: m = n = k in --split-sizes, inputs N(0,1) and N(0,1) 2^(u_r + v_c)
          (u, v integers in [-20, 20] per row and column), op N,N; TFLOP/s,
          error, speedup over the FP64 rate at the same size.
+  sliced: the digit-sliced FP64 path (FP64 data on the BF16 tensor cores),
+         m = n = k in --sliced-sizes, the --ops pairs, both layouts.
 
 Timing: CUDA events on the launching stream around `reps` calls after
 warm-up; inputs of every case are larger than L2 except the smallest FP64
@@ -53,7 +55,7 @@ def _sampled_error(opA, opB, n, alpha, beta, A, B, C0, C, layout, count=256, see
     return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
 
 
-def fp64_case(n, opA, opB, layout, peak, reps):
+def fp64_case(n, opA, opB, layout, peak, reps, precision="fp64"):
     import torch
 
     import qsynth
@@ -67,13 +69,14 @@ def fp64_case(n, opA, opB, layout, peak, reps):
     C0 = torch.randn(shape, dtype=torch.float64, device=dev, generator=gen)
     C = C0.clone()
     alpha, beta = qsynth.unit_quaternion(n + 1), qsynth.unit_quaternion(n + 2)
-    ms = _timed(lambda: ops.qgemm(opA, opB, n, n, n, alpha, A, B, beta, C, layout=layout), reps)
+    ms = _timed(lambda: ops.qgemm(opA, opB, n, n, n, alpha, A, B, beta, C, layout=layout,
+                                  precision=precision), reps)
     C.copy_(C0)
-    ops.qgemm(opA, opB, n, n, n, alpha, A, B, beta, C, layout=layout)
+    ops.qgemm(opA, opB, n, n, n, alpha, A, B, beta, C, layout=layout, precision=precision)
     torch.cuda.synchronize()
     err = _sampled_error(opA, opB, n, alpha, beta, A, B, C0, C, layout)
     tf = 32.0 * n ** 3 / (ms * 1e-3) / 1e12
-    return {"path": "fp64", "n": n, "op": opA + opB, "layout": layout, "ms": ms, "tflops": tf,
+    return {"path": precision, "n": n, "op": opA + opB, "layout": layout, "ms": ms, "tflops": tf,
             "frac_of_dmma_peak": tf / peak, "rel_err_sampled": err, "tolerance": 1e-12,
             "l2": "inputs %.2f GiB" % (3 * n * n * 32 / 2 ** 30)}
 
@@ -155,6 +158,7 @@ def main():
     ap.add_argument("--ops", default="all")
     ap.add_argument("--layouts", default="interleaved,planes")
     ap.add_argument("--split-sizes", default="2048,8192")
+    ap.add_argument("--sliced-sizes", default="")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--compare", default="", help="sizes for the cuBLAS ZGEMM/DGEMM comparison")
     a = ap.parse_args()
@@ -169,6 +173,14 @@ def main():
                 rec = fp64_case(n, op[0], op[1], layout, peak, a.reps)
                 rec["wall_s"] = time.time() - t0
                 fp64_rate[n] = rec["tflops"]
+                print(json.dumps(rec), flush=True)
+    for n in [int(x) for x in a.sliced_sizes.split(",") if x]:
+        for layout in a.layouts.split(","):
+            for op in pairs:
+                rec = fp64_case(n, op[0], op[1], layout, peak, max(a.reps, 3), "fp64_sliced")
+                rec.pop("frac_of_dmma_peak")
+                rec["issued_bf16_tflops"] = 21.0 * rec["tflops"]
+                rec["speedup_vs_dmma_path"] = rec["tflops"] / fp64_rate.get(n, peak)
                 print(json.dumps(rec), flush=True)
     for n in [int(x) for x in a.split_sizes.split(",") if x]:
         base = fp64_rate.get(n, peak)
