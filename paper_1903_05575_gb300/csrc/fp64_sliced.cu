@@ -52,6 +52,7 @@ using split::tc_fence_before;
 using split::tmem_alloc;
 using split::tmem_dealloc;
 using split::umma_bf16;
+using split::tmem_ld32;
 using split::umma_commit;
 
 constexpr int SBM = 128;        // rows of C per tile
@@ -86,8 +87,9 @@ struct SlicedParams {
 struct Ctl {
   uint64_t full[SST];
   uint64_t empty[SST];
-  uint64_t accfull;
-  uint64_t accempty;
+  uint64_t accfull;  // the MMAs of a chunk completed
+  uint64_t free23;   // drain has read levels 2, 3 (and 4, 5 after a tile's last chunk)
+  uint64_t free01;   // drain has read levels 0, 1
   uint64_t done;
   uint32_t tmem_base;
   int abort;
@@ -122,111 +124,45 @@ __device__ __forceinline__ bool tile_skip(const SlicedParams &g, int mt, int nt)
   return false;
 }
 
-// The 21 slice products of one k-step (16 real k) as 8 MMAs: A slice i
-// against B slices j0.. (adjacent in shared memory), into level regions
-// i + j0 .. (adjacent in TMEM, 64 columns each).
-__device__ __forceinline__ void mma_kstep(uint32_t d, uint32_t sa, uint32_t sb, int ks,
-                                          uint32_t acc03, uint32_t acc45) {
-  const uint32_t ka = sa + ks * 32, kb = sb + ks * 32;
-  umma_bf16(d + 0 * SBN, smem_desc_sw64(ka + 0 * kSliceA), smem_desc_sw64(kb + 0 * kSliceB),
-            idesc_bf16(SBM, 4 * SBN), acc03);                                    // 00 01 02 03
-  umma_bf16(d + 4 * SBN, smem_desc_sw64(ka + 0 * kSliceA), smem_desc_sw64(kb + 4 * kSliceB),
-            idesc_bf16(SBM, 2 * SBN), acc45);                                    // 04 05
-  umma_bf16(d + 1 * SBN, smem_desc_sw64(ka + 1 * kSliceA), smem_desc_sw64(kb + 0 * kSliceB),
-            idesc_bf16(SBM, 4 * SBN), 1u);                                       // 10 11 12 13
-  umma_bf16(d + 5 * SBN, smem_desc_sw64(ka + 1 * kSliceA), smem_desc_sw64(kb + 4 * kSliceB),
-            idesc_bf16(SBM, 1 * SBN), 1u);                                       // 14
-  umma_bf16(d + 2 * SBN, smem_desc_sw64(ka + 2 * kSliceA), smem_desc_sw64(kb + 0 * kSliceB),
-            idesc_bf16(SBM, 4 * SBN), 1u);                                       // 20 21 22 23
-  umma_bf16(d + 3 * SBN, smem_desc_sw64(ka + 3 * kSliceA), smem_desc_sw64(kb + 0 * kSliceB),
-            idesc_bf16(SBM, 3 * SBN), 1u);                                       // 30 31 32
-  umma_bf16(d + 4 * SBN, smem_desc_sw64(ka + 4 * kSliceA), smem_desc_sw64(kb + 0 * kSliceB),
-            idesc_bf16(SBM, 2 * SBN), 1u);                                       // 40 41
-  umma_bf16(d + 5 * SBN, smem_desc_sw64(ka + 5 * kSliceA), smem_desc_sw64(kb + 0 * kSliceB),
-            idesc_bf16(SBM, 1 * SBN), 1u);                                       // 50
+__device__ __forceinline__ void mma(uint32_t d, uint32_t a, uint32_t b, int n, uint32_t acc) {
+  umma_bf16(d, smem_desc_sw64(a), smem_desc_sw64(b), idesc_bf16(SBM, n), acc);
 }
 
-// One drain thread's epilogue: row i, quaternion columns nq0 .. nq0 + 7,
-// S = T + tail (in units of 2^-24 of the level-0 digit products) for the 32
-// real columns 4 (n - nq0) + c.
-__device__ __forceinline__ void epilogue(const SlicedParams &g, int64_t i, int64_t nq0,
-                                         const double (&S)[32]) {
-  if (i >= g.m) return;
-  if (g.tri == 2 && nq0 + 7 < i) return;
-  const int ea = g.eA[i];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int64_t nn = nq0 + q;
-    if (nn >= g.n) continue;
-    if ((g.tri == 1 && i < nn) || (g.tri == 2 && i > nn)) continue;
-    const int eb = g.eB[nn];
-    double P[4];
-    if (ea == kNonFinite || eb == kNonFinite) {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) P[c] = __longlong_as_double(0x7ff8000000000000ll);
-    } else {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) P[c] = ldexp(S[4 * q + c], ea + eb - 38);
-    }
-    double cin[4] = {0.0, 0.0, 0.0, 0.0};
-    double *dst0;
-    if (g.layout == QGEMM_INTERLEAVED) {
-      dst0 = g.C + 4 * (i + nn * g.ldc);
-      if (!g.beta_zero) {
-        if (g.c_vec2) {
-          const double2 lo = *reinterpret_cast<const double2 *>(dst0);
-          const double2 hi = *reinterpret_cast<const double2 *>(dst0 + 2);
-          cin[0] = lo.x; cin[1] = lo.y; cin[2] = hi.x; cin[3] = hi.y;
-        } else {
-#pragma unroll
-          for (int s = 0; s < 4; ++s) cin[s] = dst0[s];
-        }
-      }
-    } else {
-      dst0 = g.C + i + nn * g.ldc;
-      if (!g.beta_zero) {
-#pragma unroll
-        for (int s = 0; s < 4; ++s) cin[s] = dst0[s * g.psC];
-      }
-    }
-    // out = alpha P + beta C (left products): (x y)^c = sum_j sign(c^j, j) x^(c^j) y^j
-    double out[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      double acc = 0.0;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int s = c ^ j;
-        const double a = basis_sign(s, j) < 0 ? -g.alpha[s] : g.alpha[s];
-        acc = fma(a, P[j], acc);
-      }
-      if (!g.beta_zero) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int s = c ^ j;
-          const double b = basis_sign(s, j) < 0 ? -g.beta[s] : g.beta[s];
-          acc = fma(b, cin[j], acc);
-        }
-      }
-      out[c] = acc;
-    }
-    if (g.tri && i == nn) out[1] = out[2] = out[3] = 0.0;  // Hermitian diagonal is real
-    if (g.layout == QGEMM_INTERLEAVED) {
-      if (g.c_vec2) {
-        *reinterpret_cast<double2 *>(dst0) = make_double2(out[0], out[1]);
-        *reinterpret_cast<double2 *>(dst0 + 2) = make_double2(out[2], out[3]);
-      } else {
-#pragma unroll
-        for (int s = 0; s < 4; ++s) dst0[s] = out[s];
-      }
-    } else {
-#pragma unroll
-      for (int s = 0; s < 4; ++s) dst0[s * g.psC] = out[s];
-    }
+// One k-step (16 real k) of the 21 slice products, in two groups: A slice i
+// against the adjacent B slices j0.., into the adjacent level regions
+// i + j0.. (64 TMEM columns each).
+// Levels 2..5: 18 products, 6 MMAs.  Levels 2, 3 restart at a chunk's first
+// k-step, levels 4, 5 at a tile's first k-step.
+__device__ __forceinline__ void mma_levels25(uint32_t d, uint32_t ka, uint32_t kb,
+                                             bool chunk_start, bool tile_start) {
+  if (chunk_start && !tile_start) {
+    mma(d + 2 * SBN, ka, kb + 2 * kSliceB, 2 * SBN, 0u);                  // 02 03
+    mma(d + 4 * SBN, ka, kb + 4 * kSliceB, 2 * SBN, 1u);                  // 04 05
+  } else {
+    mma(d + 2 * SBN, ka, kb + 2 * kSliceB, 4 * SBN, tile_start ? 0u : 1u);  // 02 03 04 05
   }
+  mma(d + 2 * SBN, ka + 1 * kSliceA, kb + 1 * kSliceB, 4 * SBN, 1u);      // 11 12 13 14
+  mma(d + 2 * SBN, ka + 2 * kSliceA, kb, 4 * SBN, 1u);                    // 20 21 22 23
+  mma(d + 3 * SBN, ka + 3 * kSliceA, kb, 3 * SBN, 1u);                    // 30 31 32
+  mma(d + 4 * SBN, ka + 4 * kSliceA, kb, 2 * SBN, 1u);                    // 40 41
+  mma(d + 5 * SBN, ka + 5 * kSliceA, kb, 1 * SBN, 1u);                    // 50
+}
+// Levels 0, 1: 3 products, 2 MMAs; both restart at a chunk's first k-step.
+__device__ __forceinline__ void mma_levels01(uint32_t d, uint32_t ka, uint32_t kb,
+                                             bool chunk_start) {
+  mma(d, ka, kb, 2 * SBN, chunk_start ? 0u : 1u);                         // 00 01
+  mma(d + SBN, ka + kSliceA, kb, 1 * SBN, 1u);                            // 10
 }
 
-// 16 consecutive 32-bit TMEM columns of this thread's lane.
+// TMEM <-> registers, 32x32b shapes (lane = row of this thread).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
   asm volatile(
@@ -240,28 +176,126 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
-
-// T[off + q] += 2^SHIFT * v[q] for exact integers v[q].
-template <int SHIFT>
-__device__ __forceinline__ void add_level(long long (&T)[32], int off, const float (&v)[16]) {
-#pragma unroll
-  for (int q = 0; q < 16; ++q)
-    T[off + q] += static_cast<long long>(__float2int_rn(v[q])) * (1ll << SHIFT);
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15])
+      : "memory");
 }
 
-// Adds this thread's 32 columns of levels 0..3 (exact integers) to T.
-__device__ __forceinline__ void drain_levels03(uint32_t base, long long (&T)[32]) {
+// T[q] += 2^SHIFT * v[q] for exact integers v[q].
+template <int SHIFT>
+__device__ __forceinline__ void add_level(long long (&T)[32], const float (&v)[32]) {
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    float v[16];
-    tmem_ld16(base + 0 * SBN + 16 * h, v);
-    add_level<24>(T, 16 * h, v);
-    tmem_ld16(base + 1 * SBN + 16 * h, v);
-    add_level<16>(T, 16 * h, v);
-    tmem_ld16(base + 2 * SBN + 16 * h, v);
-    add_level<8>(T, 16 * h, v);
-    tmem_ld16(base + 3 * SBN + 16 * h, v);
-    add_level<0>(T, 16 * h, v);
+  for (int q = 0; q < 32; ++q)
+    T[q] += static_cast<long long>(__float2int_rn(v[q])) * (1ll << SHIFT);
+}
+
+// Keeps the compiler from sinking the adds into T below the next TMEM load
+// (which would hold two sets of loaded levels live at once).
+__device__ __forceinline__ void pin(long long (&T)[32]) {
+#pragma unroll
+  for (int q = 0; q < 32; ++q) asm volatile("" : "+l"(T[q]));
+}
+
+// x * 2^e without rounding unless the result is subnormal.
+__device__ __forceinline__ double scale2(double x, int e) {
+  if (e >= -1022 && e <= 1023) return x * __hiloint2double((e + 1023) << 20, 0);
+  return ldexp(x, e);
+}
+
+// The epilogue of quaternion column nq0 + q of row i of a finished tile:
+// S (4 doubles, units of 2^-24 of a level-0 digit product) from the spare
+// TMEM columns, P = 2^(e_i + e_n - 38) S, C <- alpha P + beta C in FP64.
+// All lanes execute the TMEM load; the rest is per lane.
+__device__ __forceinline__ void epilogue_piece(const SlicedParams &g, uint32_t spare, int64_t i,
+                                               int ea, int64_t nq0, int q) {
+  uint32_t r[8];
+  tmem_ld8(spare + 8 * q, r);
+  const int64_t nn = nq0 + q;
+  if (i >= g.m || nn >= g.n) return;
+  if ((g.tri == 1 && i < nn) || (g.tri == 2 && i > nn)) return;
+  const int eb = g.eB[nn];
+  double P[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double Sc = __hiloint2double(static_cast<int>(r[2 * c + 1]), static_cast<int>(r[2 * c]));
+    P[c] = (ea == kNonFinite || eb == kNonFinite) ? __longlong_as_double(0x7ff8000000000000ll)
+                                                  : scale2(Sc, ea + eb - 38);
+  }
+  double cin[4] = {0.0, 0.0, 0.0, 0.0};
+  double *dst0;
+  if (g.layout == QGEMM_INTERLEAVED) {
+    dst0 = g.C + 4 * (i + nn * g.ldc);
+    if (!g.beta_zero) {
+      if (g.c_vec2) {
+        const double2 lo = *reinterpret_cast<const double2 *>(dst0);
+        const double2 hi = *reinterpret_cast<const double2 *>(dst0 + 2);
+        cin[0] = lo.x; cin[1] = lo.y; cin[2] = hi.x; cin[3] = hi.y;
+      } else {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) cin[s] = dst0[s];
+      }
+    }
+  } else {
+    dst0 = g.C + i + nn * g.ldc;
+    if (!g.beta_zero) {
+#pragma unroll
+      for (int s = 0; s < 4; ++s) cin[s] = dst0[s * g.psC];
+    }
+  }
+  // out = alpha P + beta C (left products): (x y)^c = sum_j sign(c^j, j) x^(c^j) y^j
+  double out[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int s = c ^ j;
+      const double a = basis_sign(s, j) < 0 ? -g.alpha[s] : g.alpha[s];
+      acc = fma(a, P[j], acc);
+    }
+    if (!g.beta_zero) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int s = c ^ j;
+        const double b = basis_sign(s, j) < 0 ? -g.beta[s] : g.beta[s];
+        acc = fma(b, cin[j], acc);
+      }
+    }
+    out[c] = acc;
+  }
+  if (g.tri && i == nn) out[1] = out[2] = out[3] = 0.0;  // Hermitian diagonal is real
+  if (g.layout == QGEMM_INTERLEAVED) {
+    if (g.c_vec2) {
+      *reinterpret_cast<double2 *>(dst0) = make_double2(out[0], out[1]);
+      *reinterpret_cast<double2 *>(dst0 + 2) = make_double2(out[2], out[3]);
+    } else {
+#pragma unroll
+      for (int s = 0; s < 4; ++s) dst0[s] = out[s];
+    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) dst0[s * g.psC] = out[s];
+  }
+}
+
+// A finished tile whose epilogue is still (partly) pending, for one drain
+// thread: its row, first quaternion column, row exponent and progress.
+struct Pending {
+  int64_t i, nq0;
+  int ea;
+  int done;  // quaternions 0 .. done-1 written; 8 when nothing is pending
+};
+
+__device__ __forceinline__ void run_pending(const SlicedParams &g, uint32_t spare, Pending &pd,
+                                            int upto) {
+  while (pd.done < upto) {
+    epilogue_piece(g, spare, pd.i, pd.ea, pd.nq0, pd.done);
+    ++pd.done;
   }
 }
 
@@ -281,7 +315,8 @@ __global__ void __launch_bounds__(kSThreads, 1)
       mbar_init(&ctl->empty[s], 1);
     }
     mbar_init(&ctl->accfull, 1);
-    mbar_init(&ctl->accempty, kDrainWarps);
+    mbar_init(&ctl->free23, kDrainWarps);
+    mbar_init(&ctl->free01, kDrainWarps);
     mbar_init(&ctl->done, 1);
     ctl->abort = 0;
     fence_barrier_init();
@@ -325,6 +360,9 @@ __global__ void __launch_bounds__(kSThreads, 1)
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
+    // A chunk starts once the drain has read levels 2..5 of the previous one;
+    // its first stage issues the level 2..5 products of both k-steps, then
+    // waits until levels 0, 1 are read too.
     if (elect_one()) {
       const uint32_t ring_addr = smem_u32(ring);
       uint32_t s_run = 0, c_run = 0;
@@ -334,8 +372,8 @@ __global__ void __launch_bounds__(kSThreads, 1)
         tile_coords(g, t, mt, nt);
         if (tile_skip(g, mt, nt)) continue;
         for (int ch = 0; ch < nch && ok; ++ch, ++c_run) {
-          // levels 0..3 of the previous chunk (all levels after a tile) drained
-          if (!wait_phase(&ctl->accempty, (c_run & 1) ^ 1, limit_ns, ctl)) {
+          const uint32_t par = (c_run & 1) ^ 1;
+          if (!wait_phase(&ctl->free23, par, limit_ns, ctl)) {
             set_abort(ctl);
             ok = false;
             break;
@@ -352,10 +390,25 @@ __global__ void __launch_bounds__(kSThreads, 1)
             tc_fence_after();
             const uint32_t sa = ring_addr + st * kStageBytes;
             const uint32_t sb = sa + kStageA;
+            if (kb == kb0) {
 #pragma unroll
-            for (int ks = 0; ks < SBK / 16; ++ks) {
-              const bool first = kb == kb0 && ks == 0;
-              mma_kstep(tmem, sa, sb, ks, first ? 0u : 1u, (first && ch == 0) ? 0u : 1u);
+              for (int ks = 0; ks < SBK / 16; ++ks)
+                mma_levels25(tmem, sa + ks * 32, sb + ks * 32, ks == 0, ks == 0 && ch == 0);
+              if (!wait_phase(&ctl->free01, par, limit_ns, ctl)) {
+                set_abort(ctl);
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+#pragma unroll
+              for (int ks = 0; ks < SBK / 16; ++ks)
+                mma_levels01(tmem, sa + ks * 32, sb + ks * 32, ks == 0);
+            } else {
+#pragma unroll
+              for (int ks = 0; ks < SBK / 16; ++ks) {
+                mma_levels25(tmem, sa + ks * 32, sb + ks * 32, false, false);
+                mma_levels01(tmem, sa + ks * 32, sb + ks * 32, false);
+              }
             }
             umma_commit(&ctl->empty[st]);  // frees the stage when these MMAs finish
           }
@@ -368,12 +421,19 @@ __global__ void __launch_bounds__(kSThreads, 1)
     }
   } else {
     // ---------------- drain + epilogue (8 warps) ----------------
+    // Per chunk: read levels 2, 3 -> release them -> add; read levels 0, 1 ->
+    // release -> add; then a share of the previous tile's epilogue, whose S
+    // waits in the spare TMEM columns 384..511.
     const int ew = warp - 2;
     const int quad = warp & 3;  // TMEM lanes 32*quad .. +31 (hardware rule: warp % 4)
     const int half = ew >> 2;   // columns [32*half, 32*half + 32) of each level region
-    const uint32_t base = tmem + (static_cast<uint32_t>(32 * quad) << 16) + 32 * half;
+    const uint32_t lanes = static_cast<uint32_t>(32 * quad) << 16;
+    const uint32_t base = tmem + lanes + 32 * half;
+    const uint32_t spare = tmem + lanes + 6 * SBN + 64 * half;
     uint32_t c_run = 0;
     bool ok = true;
+    Pending pd{0, 0, 0, 8};
+    const int nbound = nch - 1;  // chunk ends before a tile's last
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int mt, nt;
       tile_coords(g, t, mt, nt);
@@ -381,28 +441,46 @@ __global__ void __launch_bounds__(kSThreads, 1)
       long long T[32];
 #pragma unroll
       for (int q = 0; q < 32; ++q) T[q] = 0;
-      // chunks 0 .. nch-2: levels 0..3; the last chunk also levels 4 and 5
-      for (int ch = 0; ch < nch - 1; ++ch, ++c_run) {
+      for (int ch = 0; ch < nbound; ++ch, ++c_run) {
         if (!wait_phase(&ctl->accfull, c_run & 1, limit_ns, ctl)) {
           set_abort(ctl);
           ok = false;
           break;
         }
         tc_fence_after();
-        drain_levels03(base, T);
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&ctl->accempty);
+        {
+          float v2[32], v3[32];
+          tmem_ld32(base + 2 * SBN, v2);
+          tmem_ld32(base + 3 * SBN, v3);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&ctl->free23);
+          add_level<8>(T, v2);
+          add_level<0>(T, v3);
+          pin(T);
+        }
+        {
+          float v0[32], v1[32];
+          tmem_ld32(base + 0 * SBN, v0);
+          tmem_ld32(base + 1 * SBN, v1);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&ctl->free01);
+          add_level<24>(T, v0);
+          add_level<16>(T, v1);
+          pin(T);
+        }
+        run_pending(g, spare, pd, ((ch + 1) * 8 + nbound - 1) / nbound);
       }
       if (!ok) break;
+      // last chunk: levels 4, 5 as well; then this tile's S goes to TMEM
       if (!wait_phase(&ctl->accfull, c_run & 1, limit_ns, ctl)) {
         set_abort(ctl);
         break;
       }
       ++c_run;
       tc_fence_after();
-      drain_levels03(base, T);
-      double S[32];
+      float tail[32];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         float v4[16], v5[16];
@@ -410,15 +488,44 @@ __global__ void __launch_bounds__(kSThreads, 1)
         tmem_ld16(base + 5 * SBN + 16 * h, v5);
 #pragma unroll
         for (int q = 0; q < 16; ++q)
-          S[16 * h + q] = static_cast<double>(T[16 * h + q]) +
-                          static_cast<double>(fmaf(v5[q], 0.00390625f, v4[q]) * 0.00390625f);
+          tail[16 * h + q] = fmaf(v5[q], 0.00390625f, v4[q]) * 0.00390625f;
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&ctl->accempty);
-      epilogue(g, static_cast<int64_t>(mt) * SBM + 32 * quad + lane,
-               static_cast<int64_t>(nt) * SBNQ + 8 * half, S);
+      {
+        float v[32];
+        tmem_ld32(base + 2 * SBN, v);
+        add_level<8>(T, v);
+        tmem_ld32(base + 3 * SBN, v);
+        add_level<0>(T, v);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ctl->free23);
+        tmem_ld32(base + 0 * SBN, v);
+        add_level<24>(T, v);
+        tmem_ld32(base + 1 * SBN, v);
+        add_level<16>(T, v);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ctl->free01);
+      }
+      run_pending(g, spare, pd, 8);  // the previous tile's S leaves TMEM first
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        uint32_t w[16];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const double S = static_cast<double>(T[8 * h + q]) + static_cast<double>(tail[8 * h + q]);
+          w[2 * q] = static_cast<uint32_t>(__double2loint(S));
+          w[2 * q + 1] = static_cast<uint32_t>(__double2hiint(S));
+        }
+        tmem_st16(spare + 16 * h, w);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      pd.i = static_cast<int64_t>(mt) * SBM + 32 * quad + lane;
+      pd.nq0 = static_cast<int64_t>(nt) * SBNQ + 8 * half;
+      pd.ea = pd.i < g.m ? g.eA[pd.i] : 0;
+      pd.done = 0;
     }
+    run_pending(g, spare, pd, 8);
   }
 
   tc_fence_before();
