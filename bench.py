@@ -389,7 +389,7 @@ def grouped_section(count, steps=5, seed=1907, dtype="fp64"):
     dev = torch.device("cuda", torch.cuda.current_device())
     gen = torch.Generator(device=dev)
     gen.manual_seed(seed)
-    tdt = torch.float64 if dtype == "fp64" else torch.float32
+    tdt = torch.float32 if dtype == "split_bf16" else torch.float64
     probs = qsynth.grouped_problems(count, seed)
     batch = []
     flops = 0.0
@@ -403,7 +403,7 @@ def grouped_section(count, steps=5, seed=1907, dtype="fp64"):
         flops += 32.0 * p["m"] * p["n"] * p["k"]
     C0 = [b["C"].clone() for b in batch]
     t0 = time.perf_counter()
-    gb = GroupedBatch(batch)
+    gb = GroupedBatch(batch, precision=dtype)
     prep_ms = 1e3 * (time.perf_counter() - t0)
     stream = torch.cuda.Stream()
     torch.cuda.synchronize()
@@ -443,7 +443,7 @@ def grouped_section(count, steps=5, seed=1907, dtype="fp64"):
             "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_launch": ms,
             "flops_per_launch": flops, "tiles": int(gb.plan.tiles), "grid": int(gb.plan.grid),
             "prepare_ms_host": prep_ms, "rel_err_sampled_worst": worst,
-            "tolerance": 1e-12 if dtype == "fp64" else 2e-6,
+            "tolerance": 2e-6 if dtype == "split_bf16" else 1e-12,
             "workspace_bytes": int(gb.ws.numel())}
 
 
@@ -639,11 +639,13 @@ def run_ours(args):
         G = qs.components(got, m, layout)[rows, cols]
         err = float(np.linalg.norm(G - ref) / np.linalg.norm(ref))
 
-    grouped = grouped_split = None
+    grouped = grouped_split = grouped_sliced = None
     if not args.no_grouped:
         grouped = grouped_section(args.grouped_count)
         grouped["frac_of_dmma_peak"] = grouped["value"] / dmma_peak
         grouped_split = grouped_section(args.grouped_count, dtype="split_bf16", seed=1908)
+        grouped_sliced = grouped_section(args.grouped_count, dtype="fp64_sliced")
+        grouped_sliced["speedup_vs_grouped_fp64"] = grouped_sliced["value"] / grouped["value"]
 
     split = None
     if not args.no_split:
@@ -679,6 +681,7 @@ def run_ours(args):
         "fp64_sliced_bf16": sliced,
         "grouped_fp64": grouped,
         "grouped_split_bf16": grouped_split,
+        "grouped_fp64_sliced_bf16": grouped_sliced,
     }
     print(json.dumps(line), flush=True)
 

@@ -35,6 +35,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "split_core.cuh"
 
@@ -77,11 +78,47 @@ struct SlicedParams {
   int64_t m, n;
   int num_kb, num_mt, num_nt;
   int layout, beta_zero, tri, c_vec2;
+  int swap;       // 1: the kernel computes D = (op(A) op(B))^H; store C = conj(D)^T
+  int alpha_real, beta_real;  // scalars with zero vector part: 4 FP64 products, not 16
   double *C;
   int64_t ldc, psC;
   double alpha[4], beta[4];
   const int *eA;  // per quaternion row of op(A)
   const int *eB;  // per quaternion column of op(B)
+};
+
+// Pre-pass arguments of one operand.
+struct MaxArgs {
+  const double *X;
+  int64_t ld, ps;        // stored leading dimension, plane stride
+  int64_t srows, scols;  // stored extent
+  int layout;
+  int by_col;            // 0: maxima per stored row, 1: per stored column
+  unsigned long long *out;
+};
+
+struct SliceArgs {
+  const double *X;
+  int64_t ld, ps;        // stored leading dimension, plane stride
+  int64_t rows;          // rows of the op-matrix (m for A, n for B)
+  int64_t kq;            // quaternion K
+  int64_t kp;            // padded real K (multiple of SBK)
+  int64_t slice_stride;  // elements between slices in the output
+  __nv_bfloat16 *out;
+  const unsigned long long *maxbits;  // per op row
+  int *eout;                          // per op row: the exponent used
+  int layout;
+  int row_contig;        // stored row index == op row
+  uint32_t negmask;      // bit j: negate component j (conjugation)
+};
+
+// One problem of a grouped batch (device descriptor in the workspace).
+struct alignas(128) SlicedProb {
+  CUtensorMap tmA;  // A' slices: (kp, m, 6) bf16
+  CUtensorMap tmB;  // B' slices: (kp, 4n, 6) bf16
+  SlicedParams g;
+  MaxArgs ma, mb;
+  SliceArgs sa, sb;
 };
 
 struct Ctl {
@@ -218,18 +255,30 @@ __device__ __forceinline__ void epilogue_piece(const SlicedParams &g, uint32_t s
   const int64_t nn = nq0 + q;
   if (i >= g.m || nn >= g.n) return;
   if ((g.tri == 1 && i < nn) || (g.tri == 2 && i > nn)) return;
-  const int eb = g.eB[nn];
-  double P[4];
+  double P[4] = {0.0, 0.0, 0.0, 0.0};
+  if (g.num_kb > 0) {  // k = 0 (or alpha = 0) in a grouped batch: C <- beta C
+    const int eb = g.eB[nn];
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const double Sc = __hiloint2double(static_cast<int>(r[2 * c + 1]), static_cast<int>(r[2 * c]));
-    P[c] = (ea == kNonFinite || eb == kNonFinite) ? __longlong_as_double(0x7ff8000000000000ll)
-                                                  : scale2(Sc, ea + eb - 38);
+    for (int c = 0; c < 4; ++c) {
+      const double Sc =
+          __hiloint2double(static_cast<int>(r[2 * c + 1]), static_cast<int>(r[2 * c]));
+      P[c] = (ea == kNonFinite || eb == kNonFinite) ? __longlong_as_double(0x7ff8000000000000ll)
+                                                    : scale2(Sc, ea + eb - 38);
+    }
+  }
+  // element (ci, cj) of C; a transposed problem holds (AB)^H: take conj(D)^T
+  int64_t ci = i, cj = nn;
+  if (g.swap) {
+    ci = nn;
+    cj = i;
+    P[1] = -P[1];
+    P[2] = -P[2];
+    P[3] = -P[3];
   }
   double cin[4] = {0.0, 0.0, 0.0, 0.0};
   double *dst0;
   if (g.layout == QGEMM_INTERLEAVED) {
-    dst0 = g.C + 4 * (i + nn * g.ldc);
+    dst0 = g.C + 4 * (ci + cj * g.ldc);
     if (!g.beta_zero) {
       if (g.c_vec2) {
         const double2 lo = *reinterpret_cast<const double2 *>(dst0);
@@ -241,7 +290,7 @@ __device__ __forceinline__ void epilogue_piece(const SlicedParams &g, uint32_t s
       }
     }
   } else {
-    dst0 = g.C + i + nn * g.ldc;
+    dst0 = g.C + ci + cj * g.ldc;
     if (!g.beta_zero) {
 #pragma unroll
       for (int s = 0; s < 4; ++s) cin[s] = dst0[s * g.psC];
@@ -252,18 +301,26 @@ __device__ __forceinline__ void epilogue_piece(const SlicedParams &g, uint32_t s
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     double acc = 0.0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int s = c ^ j;
-      const double a = basis_sign(s, j) < 0 ? -g.alpha[s] : g.alpha[s];
-      acc = fma(a, P[j], acc);
-    }
-    if (!g.beta_zero) {
+    if (g.alpha_real) {
+      acc = g.alpha[0] * P[c];
+    } else {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int s = c ^ j;
-        const double b = basis_sign(s, j) < 0 ? -g.beta[s] : g.beta[s];
-        acc = fma(b, cin[j], acc);
+        const double a = basis_sign(s, j) < 0 ? -g.alpha[s] : g.alpha[s];
+        acc = fma(a, P[j], acc);
+      }
+    }
+    if (!g.beta_zero) {
+      if (g.beta_real) {
+        acc = fma(g.beta[0], cin[c], acc);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int s = c ^ j;
+          const double b = basis_sign(s, j) < 0 ? -g.beta[s] : g.beta[s];
+          acc = fma(b, cin[j], acc);
+        }
       }
     }
     out[c] = acc;
@@ -286,23 +343,50 @@ __device__ __forceinline__ void epilogue_piece(const SlicedParams &g, uint32_t s
 // A finished tile whose epilogue is still (partly) pending, for one drain
 // thread: its row, first quaternion column, row exponent and progress.
 struct Pending {
+  const SlicedParams *g;
   int64_t i, nq0;
   int ea;
   int done;  // quaternions 0 .. done-1 written; 8 when nothing is pending
 };
 
-__device__ __forceinline__ void run_pending(const SlicedParams &g, uint32_t spare, Pending &pd,
-                                            int upto) {
+__device__ __forceinline__ void run_pending(uint32_t spare, Pending &pd, int upto) {
   while (pd.done < upto) {
-    epilogue_piece(g, spare, pd.i, pd.ea, pd.nq0, pd.done);
+    epilogue_piece(*pd.g, spare, pd.i, pd.ea, pd.nq0, pd.done);
     ++pd.done;
   }
 }
 
+// Tile t -> problem parameters, tensor maps and tile coordinates.  Single
+// problem: rasterised in groups of kGroupM row tiles; grouped: tiles[t] =
+// (problem, row tile, column tile).
+template <bool GROUPED>
+__device__ __forceinline__ void tile_of(int t, const SlicedParams &single, const CUtensorMap *smA,
+                                        const CUtensorMap *smB, const SlicedProb *probs,
+                                        const int4 *tiles, const SlicedParams *&g,
+                                        const CUtensorMap *&mA, const CUtensorMap *&mB, int &mt,
+                                        int &nt) {
+  if (GROUPED) {
+    const int4 e = tiles[t];
+    const SlicedProb *pr = probs + e.x;
+    g = &pr->g;
+    mA = &pr->tmA;
+    mB = &pr->tmB;
+    mt = e.y;
+    nt = e.z;
+  } else {
+    g = &single;
+    mA = smA;
+    mB = smB;
+    tile_coords(single, t, mt, nt);
+  }
+}
+
+template <bool GROUPED>
 __global__ void __launch_bounds__(kSThreads, 1)
     sliced_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
-                       const __grid_constant__ CUtensorMap tmB, const SlicedParams g, int ntiles,
-                       uint64_t limit_ns) {
+                       const __grid_constant__ CUtensorMap tmB, const SlicedParams single,
+                       const SlicedProb *__restrict__ probs, const int4 *__restrict__ tiles,
+                       int ntiles, uint64_t limit_ns) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t raw_addr = smem_u32(smem_raw);
   unsigned char *ring = smem_raw + ((1024 - (raw_addr & 1023)) & 1023);
@@ -326,20 +410,23 @@ __global__ void __launch_bounds__(kSThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = ctl->tmem_base;
-  const int nkb = g.num_kb;
-  const int nch = (nkb + kChunkKb - 1) / kChunkKb;
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (elect_one()) {
-      tma_prefetch_desc(&tmA);
-      tma_prefetch_desc(&tmB);
+      if (!GROUPED) {
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmB);
+      }
       uint32_t s_run = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const SlicedParams *g;
+        const CUtensorMap *mA, *mB;
         int mt, nt;
-        tile_coords(g, t, mt, nt);
-        if (tile_skip(g, mt, nt)) continue;
+        tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt);
+        if (tile_skip(*g, mt, nt)) continue;
+        const int nkb = g->num_kb;
         for (int kb = 0; kb < nkb; ++kb, ++s_run) {
           const int st = s_run % SST;
           if (!wait_phase(&ctl->empty[st], ((s_run / SST) & 1) ^ 1, limit_ns, ctl)) {
@@ -349,8 +436,8 @@ __global__ void __launch_bounds__(kSThreads, 1)
           }
           unsigned char *sa = ring + st * kStageBytes;
           mbar_arrive_expect_tx(&ctl->full[st], kStageBytes);
-          tma_load_3d(sa, &tmA, &ctl->full[st], kb * SBK, mt * SBM, 0);
-          tma_load_3d(sa + kStageA, &tmB, &ctl->full[st], kb * SBK, nt * SBN, 0);
+          tma_load_3d(sa, mA, &ctl->full[st], kb * SBK, mt * SBM, 0);
+          tma_load_3d(sa + kStageA, mB, &ctl->full[st], kb * SBK, nt * SBN, 0);
         }
       }
       if (!ok) {  // let this CTA's copies in flight land before it retires
@@ -368,9 +455,13 @@ __global__ void __launch_bounds__(kSThreads, 1)
       uint32_t s_run = 0, c_run = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const SlicedParams *g;
+        const CUtensorMap *mA, *mB;
         int mt, nt;
-        tile_coords(g, t, mt, nt);
-        if (tile_skip(g, mt, nt)) continue;
+        tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt);
+        if (tile_skip(*g, mt, nt)) continue;
+        const int nkb = g->num_kb;
+        const int nch = (nkb + kChunkKb - 1) / kChunkKb;
         for (int ch = 0; ch < nch && ok; ++ch, ++c_run) {
           const uint32_t par = (c_run & 1) ^ 1;
           if (!wait_phase(&ctl->free23, par, limit_ns, ctl)) {
@@ -432,12 +523,15 @@ __global__ void __launch_bounds__(kSThreads, 1)
     const uint32_t spare = tmem + lanes + 6 * SBN + 64 * half;
     uint32_t c_run = 0;
     bool ok = true;
-    Pending pd{0, 0, 0, 8};
-    const int nbound = nch - 1;  // chunk ends before a tile's last
+    Pending pd{nullptr, 0, 0, 0, 8};
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const SlicedParams *g;
+      const CUtensorMap *mA, *mB;
       int mt, nt;
-      tile_coords(g, t, mt, nt);
-      if (tile_skip(g, mt, nt)) continue;
+      tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt);
+      if (tile_skip(*g, mt, nt)) continue;
+      const int nch = (g->num_kb + kChunkKb - 1) / kChunkKb;
+      const int nbound = nch - 1;  // chunk ends before the tile's last
       long long T[32];
 #pragma unroll
       for (int q = 0; q < 32; ++q) T[q] = 0;
@@ -470,27 +564,30 @@ __global__ void __launch_bounds__(kSThreads, 1)
           add_level<16>(T, v1);
           pin(T);
         }
-        run_pending(g, spare, pd, ((ch + 1) * 8 + nbound - 1) / nbound);
+        run_pending(spare, pd, ((ch + 1) * 8 + nbound - 1) / nbound);
       }
       if (!ok) break;
       // last chunk: levels 4, 5 as well; then this tile's S goes to TMEM
-      if (!wait_phase(&ctl->accfull, c_run & 1, limit_ns, ctl)) {
-        set_abort(ctl);
-        break;
-      }
-      ++c_run;
-      tc_fence_after();
+      // (no chunk at all for k = 0 in a grouped batch)
       float tail[32];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        float v4[16], v5[16];
-        tmem_ld16(base + 4 * SBN + 16 * h, v4);
-        tmem_ld16(base + 5 * SBN + 16 * h, v5);
+      for (int q = 0; q < 32; ++q) tail[q] = 0.f;
+      if (nch > 0) {
+        if (!wait_phase(&ctl->accfull, c_run & 1, limit_ns, ctl)) {
+          set_abort(ctl);
+          break;
+        }
+        ++c_run;
+        tc_fence_after();
 #pragma unroll
-        for (int q = 0; q < 16; ++q)
-          tail[16 * h + q] = fmaf(v5[q], 0.00390625f, v4[q]) * 0.00390625f;
-      }
-      {
+        for (int h = 0; h < 2; ++h) {
+          float v4[16], v5[16];
+          tmem_ld16(base + 4 * SBN + 16 * h, v4);
+          tmem_ld16(base + 5 * SBN + 16 * h, v5);
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            tail[16 * h + q] = fmaf(v5[q], 0.00390625f, v4[q]) * 0.00390625f;
+        }
         float v[32];
         tmem_ld32(base + 2 * SBN, v);
         add_level<8>(T, v);
@@ -507,7 +604,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&ctl->free01);
       }
-      run_pending(g, spare, pd, 8);  // the previous tile's S leaves TMEM first
+      run_pending(spare, pd, 8);  // the previous tile's S leaves TMEM first
 #pragma unroll
       for (int h = 0; h < 4; ++h) {
         uint32_t w[16];
@@ -520,12 +617,13 @@ __global__ void __launch_bounds__(kSThreads, 1)
         tmem_st16(spare + 16 * h, w);
       }
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      pd.g = g;
       pd.i = static_cast<int64_t>(mt) * SBM + 32 * quad + lane;
       pd.nq0 = static_cast<int64_t>(nt) * SBNQ + 8 * half;
-      pd.ea = pd.i < g.m ? g.eA[pd.i] : 0;
+      pd.ea = pd.i < g->m ? g->eA[pd.i] : 0;
       pd.done = 0;
     }
-    run_pending(g, spare, pd, 8);
+    run_pending(spare, pd, 8);
   }
 
   tc_fence_before();
@@ -539,49 +637,66 @@ __global__ void __launch_bounds__(kSThreads, 1)
 // ------------------------------------------------------------ pre-pass ---
 // Largest |component| of each quaternion row (by_col = 0) or column
 // (by_col = 1) of a stored matrix, as the bits of a non-negative double
-// (ordered like the values; NaN above Inf), max-reduced into out[].
-__global__ void __launch_bounds__(256)
-    slice_max_kernel(const double *__restrict__ X, int64_t ld, int64_t ps, int64_t srows,
-                     int64_t scols, int layout, int by_col, unsigned long long *out) {
-  __shared__ unsigned long long red[8][32];
+// (ordered like the values; NaN above Inf), max-reduced into out[]: one
+// 32 x 32 tile (rt, ct) of the stored matrix per call, 256 threads.
+__device__ __forceinline__ void max_tile(const MaxArgs &a, int64_t rt, int64_t ct,
+                                         unsigned long long (*red)[32]) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int64_t r = static_cast<int64_t>(blockIdx.x) * 32 + tx;
-  const int64_t c0 = static_cast<int64_t>(blockIdx.y) * 32;
+  const int64_t r = rt * 32 + tx;
+  const int64_t c0 = ct * 32;
   unsigned long long rowm = 0;
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     const int64_t c = c0 + ty + 8 * s;
     unsigned long long mx = 0;
-    if (r < srows && c < scols) {
+    if (r < a.srows && c < a.scols) {
 #pragma unroll
       for (int comp = 0; comp < 4; ++comp) {
-        const double x = layout == QGEMM_INTERLEAVED ? X[4 * (r + c * ld) + comp]
-                                                     : X[r + c * ld + comp * ps];
+        const double x = a.layout == QGEMM_INTERLEAVED ? a.X[4 * (r + c * a.ld) + comp]
+                                                       : a.X[r + c * a.ld + comp * a.ps];
         const unsigned long long b =
             static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7fffffffffffffffull;
         mx = b > mx ? b : mx;
       }
     }
-    if (by_col) {
+    if (a.by_col) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
         mx = y > mx ? y : mx;
       }
-      if (tx == 0 && c < scols && mx != 0) atomicMax(out + c, mx);
+      if (tx == 0 && c < a.scols && mx != 0) atomicMax(a.out + c, mx);
     } else {
       rowm = mx > rowm ? mx : rowm;
     }
   }
-  if (!by_col) {
+  if (!a.by_col) {
     red[ty][tx] = rowm;
     __syncthreads();
     if (ty == 0) {
       unsigned long long v = red[0][tx];
 #pragma unroll
       for (int w = 1; w < 8; ++w) v = red[w][tx] > v ? red[w][tx] : v;
-      if (r < srows && v != 0) atomicMax(out + r, v);
+      if (r < a.srows && v != 0) atomicMax(a.out + r, v);
     }
+  }
+}
+
+__global__ void __launch_bounds__(256) slice_max_kernel(const MaxArgs a) {
+  __shared__ unsigned long long red[8][32];
+  max_tile(a, blockIdx.x, blockIdx.y, red);
+}
+
+// Grouped: mtiles[t] = (problem, operand 0 A / 1 B, row tile, column tile).
+__global__ void __launch_bounds__(256)
+    grouped_slice_max_kernel(const SlicedProb *__restrict__ probs,
+                             const int4 *__restrict__ mtiles, int n) {
+  __shared__ unsigned long long red[8][32];
+  for (int t = blockIdx.x; t < n; t += gridDim.x) {
+    const int4 e = mtiles[t];
+    const SlicedProb &pr = probs[e.x];
+    max_tile(e.y ? pr.mb : pr.ma, e.z, e.w, red);
+    __syncthreads();
   }
 }
 
@@ -594,24 +709,37 @@ __device__ __forceinline__ int exponent_of(unsigned long long maxbits) {
   return e;
 }
 
-struct SliceArgs {
-  const double *X;
-  int64_t ld, ps;        // stored leading dimension, plane stride
-  int64_t rows;          // rows of the op-matrix (m for A, n for B)
-  int64_t kq;            // quaternion K
-  int64_t kp;            // padded real K (multiple of SBK)
-  int64_t slice_stride;  // elements between slices in the output
-  __nv_bfloat16 *out;
-  const unsigned long long *maxbits;  // per op row
-  int *eout;                          // per op row: the exponent used
-  int layout;
-  int row_contig;        // stored row index == op row
-  uint32_t negmask;      // bit j: negate component j (conjugation)
-};
 
-// Balanced base-256 digits of round(x) for |x| <= 2^47: x ~ sum d_t 2^(8 (5 - t)).
-__device__ __forceinline__ void digits6(double x, int (&d)[NSL]) {
-  long long X = __double2ll_rn(x);
+// round(a 2^s) to the nearest integer (ties to even) for |a| 2^s <= 2^47,
+// from the bits of a: integer operations only (GB300's FP64 pipe is narrow).
+__device__ __forceinline__ long long round_scaled(double a, int s) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(a));
+  const int E = static_cast<int>((b >> 52) & 0x7ff);
+  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  int e2;  // |a| = m 2^e2
+  if (E == 0) {
+    e2 = -1074;
+  } else {
+    m |= 1ull << 52;
+    e2 = E - 1075;
+  }
+  const int sh = -(e2 + s);  // |a| 2^s = m 2^-sh
+  long long q;
+  if (sh <= 0) {
+    q = static_cast<long long>(m << (-sh));
+  } else if (sh >= 64) {
+    q = 0;  // m < 2^53 <= 2^(sh-1): below one half
+  } else {
+    const unsigned long long qq = m >> sh;
+    const unsigned long long rem = m & ((1ull << sh) - 1);
+    const unsigned long long half = 1ull << (sh - 1);
+    q = static_cast<long long>(qq + ((rem > half || (rem == half && (qq & 1))) ? 1 : 0));
+  }
+  return (b >> 63) ? -q : q;
+}
+
+// Balanced base-256 digits of X, |X| <= 2^47: X = sum d_t 2^(8 (5 - t)).
+__device__ __forceinline__ void digits6(long long X, int (&d)[NSL]) {
 #pragma unroll
   for (int t = NSL - 1; t >= 1; --t) {
     const long long lo = ((X + 128) & 255) - 128;
@@ -626,26 +754,26 @@ __device__ __forceinline__ void digits6(double x, int (&d)[NSL]) {
 //   A: A'_t[r][4 kappa + j] = d_t(a^j)
 //   B: B'_t[4 r + c][4 kappa + j] = sign(j, j^c) d_t(b^(j^c))
 // Columns kappa >= kq up to kp/4 are zeros (K padding).
+struct SliceSmem {
+  double4 tile[32][33];
+  int shift[32];  // 47 - e of each row; kNonFinite for a row with Inf or NaN
+};
+
 template <bool IS_B>
-__global__ void __launch_bounds__(256) slice_kernel(const SliceArgs p) {
-  __shared__ double4 tile[32][33];
-  __shared__ double scale1[32], scale2[32];
+__device__ __forceinline__ void slice_tile(const SliceArgs &p, int64_t rt, int64_t kt,
+                                           SliceSmem &sm) {
+  double4 (*tile)[33] = sm.tile;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 32;
-  const int64_t k0 = static_cast<int64_t>(blockIdx.y) * 32;
+  const int64_t r0 = rt * 32;
+  const int64_t k0 = kt * 32;
   if (threadIdx.x < 32) {
     const int64_t r = r0 + threadIdx.x;
     int e = 0;
     if (r < p.rows) {
       e = exponent_of(p.maxbits[r]);
-      if (blockIdx.y == 0) p.eout[r] = e;
+      if (kt == 0) p.eout[r] = e;
     }
-    // x = a 2^(47 - e) as two exact power-of-two factors (each in range)
-    const int s = e == kNonFinite ? 0 : 47 - e;
-    const int s1 = s > 1000 ? 1000 : (s < -1000 ? -1000 : s);
-    scale1[threadIdx.x] = ldexp(1.0, s1);
-    scale2[threadIdx.x] = ldexp(1.0, s - s1);
-    if (e == kNonFinite) scale1[threadIdx.x] = 0.0;
+    sm.shift[threadIdx.x] = e == kNonFinite ? kNonFinite : 47 - e;
   }
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
@@ -676,16 +804,12 @@ __global__ void __launch_bounds__(256) slice_kernel(const SliceArgs p) {
     const int64_t r = r0 + rr, kq = k0 + kk;
     if (r >= p.rows || 4 * kq >= p.kp) continue;
     const double4 v = tile[kk][rr];
-    const double f1 = scale1[rr], f2 = scale2[rr];
+    const int sft = sm.shift[rr];
     const double comp[4] = {v.x, v.y, v.z, v.w};
     int d[4][NSL];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      double x = comp[j] * f1;
-      x *= f2;
-      if (!(fabs(x) <= 140737488355328.0)) x = 0.0;  // non-finite row: digits 0, C gets NaN
-      digits6(x, d[j]);
-    }
+    for (int j = 0; j < 4; ++j)  // a non-finite row gets digits 0 (its C entries NaN)
+      digits6(sft == kNonFinite ? 0ll : round_scaled(comp[j], sft), d[j]);
     if (!IS_B) {
 #pragma unroll
       for (int t = 0; t < NSL; ++t) {
@@ -711,6 +835,28 @@ __global__ void __launch_bounds__(256) slice_kernel(const SliceArgs p) {
           *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(w);
         }
     }
+  }
+}
+
+template <bool IS_B>
+__global__ void __launch_bounds__(256) slice_kernel(const SliceArgs p) {
+  __shared__ SliceSmem sm;
+  slice_tile<IS_B>(p, blockIdx.x, blockIdx.y, sm);
+}
+
+// Grouped: stiles[t] = (problem, operand 0 A / 1 B, row tile, k tile).
+__global__ void __launch_bounds__(256)
+    grouped_slice_kernel(const SlicedProb *__restrict__ probs, const int4 *__restrict__ stiles,
+                         int n) {
+  __shared__ SliceSmem sm;
+  for (int t = blockIdx.x; t < n; t += gridDim.x) {
+    const int4 e = stiles[t];
+    const SlicedProb &pr = probs[e.x];
+    if (e.y)
+      slice_tile<true>(pr.sb, e.z, e.w, sm);
+    else
+      slice_tile<false>(pr.sa, e.z, e.w, sm);
+    __syncthreads();
   }
 }
 
@@ -752,20 +898,22 @@ bool encode_slices(CUtensorMap *map, const void *base, int64_t kp, int64_t rows,
   return r == CUDA_SUCCESS;
 }
 
-int launch_max(const MatView &v, bool by_col, int layout, unsigned long long *out,
-               cudaStream_t stream) {
-  const int64_t gx = (v.rows + 31) / 32, gy = (v.cols + 31) / 32;
-  if (gx == 0 || gy == 0) return QGEMM_SUCCESS;
-  if (gx > 0x7fffffff || gy > 65535) return QGEMM_ERR_UNSUPPORTED;
-  slice_max_kernel<<<dim3(static_cast<unsigned>(gx), static_cast<unsigned>(gy)), 256, 0,
-                     stream>>>(static_cast<const double *>(v.ptr), v.ld, v.ps, v.rows, v.cols,
-                               layout, by_col ? 1 : 0, out);
-  return launch_status();
+MaxArgs max_args(const MatView &v, bool by_col, int layout, unsigned long long *out) {
+  MaxArgs a;
+  a.X = static_cast<const double *>(v.ptr);
+  a.ld = v.ld;
+  a.ps = v.ps;
+  a.srows = v.rows;
+  a.scols = v.cols;
+  a.layout = layout;
+  a.by_col = by_col ? 1 : 0;
+  a.out = out;
+  return a;
 }
 
-int launch_slices(bool is_b, const MatView &v, int op, int64_t rows, int64_t kq, int64_t kp,
-                  int layout, __nv_bfloat16 *out, int64_t slice_stride,
-                  const unsigned long long *maxbits, int *eout, cudaStream_t stream) {
+SliceArgs slice_args(bool is_b, const MatView &v, int op, int64_t rows, int64_t kq, int64_t kp,
+                     int layout, __nv_bfloat16 *out, const unsigned long long *maxbits,
+                     int *eout) {
   SliceArgs a;
   a.X = static_cast<const double *>(v.ptr);
   a.ld = v.ld;
@@ -773,14 +921,31 @@ int launch_slices(bool is_b, const MatView &v, int op, int64_t rows, int64_t kq,
   a.rows = rows;
   a.kq = kq;
   a.kp = kp;
-  a.slice_stride = slice_stride;
+  a.slice_stride = (is_b ? 4 * rows : rows) * kp;
   a.out = out;
   a.maxbits = maxbits;
   a.eout = eout;
   a.layout = layout;
   a.row_contig = is_b ? (op_trans(op) ? 1 : 0) : (op_trans(op) ? 0 : 1);
   a.negmask = op_conj(op) ? 0xEu : 0u;
-  const int64_t gx = (rows + 31) / 32, gy = (kp / 4 + 31) / 32;
+  return a;
+}
+
+// Row maxima of op(A): stored rows for N/C, stored columns for T/H; column
+// maxima of op(B): stored columns for N/C, stored rows for T/H.
+bool max_by_col(bool is_b, int op) { return is_b ? !op_trans(op) : op_trans(op); }
+
+int launch_max(const MaxArgs &a, cudaStream_t stream) {
+  const int64_t gx = (a.srows + 31) / 32, gy = (a.scols + 31) / 32;
+  if (gx == 0 || gy == 0) return QGEMM_SUCCESS;
+  if (gx > 0x7fffffff || gy > 65535) return QGEMM_ERR_UNSUPPORTED;
+  slice_max_kernel<<<dim3(static_cast<unsigned>(gx), static_cast<unsigned>(gy)), 256, 0,
+                     stream>>>(a);
+  return launch_status();
+}
+
+int launch_slices(bool is_b, const SliceArgs &a, cudaStream_t stream) {
+  const int64_t gx = (a.rows + 31) / 32, gy = (a.kp / 4 + 31) / 32;
   if (gx > 0x7fffffff || gy > 65535) return QGEMM_ERR_UNSUPPORTED;
   dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy));
   if (is_b)
@@ -788,6 +953,55 @@ int launch_slices(bool is_b, const MatView &v, int op, int64_t rows, int64_t kq,
   else
     slice_kernel<false><<<grid, 256, 0, stream>>>(a);
   return launch_status();
+}
+
+SlicedParams params_for(const GemmDesc &d, int64_t kp, const int *ea, const int *eb) {
+  SlicedParams g{};
+  g.m = d.m;
+  g.n = d.n;
+  g.num_kb = static_cast<int>(d.k > 0 ? kp / SBK : 0);
+  g.num_mt = static_cast<int>((d.m + SBM - 1) / SBM);
+  g.num_nt = static_cast<int>((d.n + SBNQ - 1) / SBNQ);
+  g.layout = d.layout;
+  g.beta_zero = d.beta_zero ? 1 : 0;
+  g.tri = d.tri;
+  g.swap = 0;
+  g.alpha_real = (d.alpha[1] == 0.0 && d.alpha[2] == 0.0 && d.alpha[3] == 0.0) ? 1 : 0;
+  g.beta_real = (d.beta[1] == 0.0 && d.beta[2] == 0.0 && d.beta[3] == 0.0) ? 1 : 0;
+  g.c_vec2 = (reinterpret_cast<uintptr_t>(d.C) % 16 == 0) ? 1 : 0;
+  g.C = static_cast<double *>(d.C);
+  g.ldc = d.ldc;
+  g.psC = d.psc;
+  for (int s = 0; s < 4; ++s) {
+    g.alpha[s] = d.alpha[s];
+    g.beta[s] = d.beta[s];
+  }
+  g.eA = ea;
+  g.eB = eb;
+  return g;
+}
+
+template <bool GROUPED>
+int set_gemm_smem() {
+  static bool done[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return QGEMM_ERR_UNSUPPORTED;
+  if (!done[dev]) {
+    if (cudaFuncSetAttribute(sliced_gemm_kernel<GROUPED>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kSmem)) != cudaSuccess)
+      return launch_status();
+    done[dev] = true;
+  }
+  return QGEMM_SUCCESS;
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
 }
 
 }  // namespace
@@ -810,16 +1024,14 @@ int launch_sliced_gemm(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_
 
   if (cudaMemsetAsync(w + pl.maxa_off, 0, pl.ea_off - pl.maxa_off, stream) != cudaSuccess)
     return launch_status();
-  // row maxima of op(A): stored rows for N/C, stored columns for T/H;
-  // column maxima of op(B): stored columns for N/C, stored rows for T/H
-  int rc = launch_max(d.A, op_trans(d.opA), d.layout, maxa, stream);
+  int rc = launch_max(max_args(d.A, max_by_col(false, d.opA), d.layout, maxa), stream);
   if (rc) return rc;
-  rc = launch_max(d.B, !op_trans(d.opB), d.layout, maxb, stream);
+  rc = launch_max(max_args(d.B, max_by_col(true, d.opB), d.layout, maxb), stream);
   if (rc) return rc;
-  rc = launch_slices(false, d.A, d.opA, d.m, d.k, pl.kp, d.layout, wa, d.m * pl.kp, maxa, ea,
+  rc = launch_slices(false, slice_args(false, d.A, d.opA, d.m, d.k, pl.kp, d.layout, wa, maxa, ea),
                      stream);
   if (rc) return rc;
-  rc = launch_slices(true, d.B, d.opB, d.n, d.k, pl.kp, d.layout, wb, 4 * d.n * pl.kp, maxb, eb,
+  rc = launch_slices(true, slice_args(true, d.B, d.opB, d.n, d.k, pl.kp, d.layout, wb, maxb, eb),
                      stream);
   if (rc) return rc;
 
@@ -828,41 +1040,232 @@ int launch_sliced_gemm(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_
   std::memset(&tmB, 0, sizeof(tmB));
   if (!encode_slices(&tmA, wa, pl.kp, d.m, SBM) || !encode_slices(&tmB, wb, pl.kp, 4 * d.n, SBN))
     return QGEMM_ERR_UNSUPPORTED;
-  SlicedParams g{};
-  g.m = d.m;
-  g.n = d.n;
-  g.num_kb = static_cast<int>(pl.kp / SBK);
-  g.num_mt = static_cast<int>((d.m + SBM - 1) / SBM);
-  g.num_nt = static_cast<int>((d.n + SBNQ - 1) / SBNQ);
-  g.layout = d.layout;
-  g.beta_zero = d.beta_zero ? 1 : 0;
-  g.tri = d.tri;
-  g.c_vec2 = (reinterpret_cast<uintptr_t>(d.C) % 16 == 0) ? 1 : 0;
-  g.C = static_cast<double *>(d.C);
-  g.ldc = d.ldc;
-  g.psC = d.psc;
-  for (int s = 0; s < 4; ++s) {
-    g.alpha[s] = d.alpha[s];
-    g.beta[s] = d.beta[s];
-  }
-  g.eA = ea;
-  g.eB = eb;
+  const SlicedParams g = params_for(d, pl.kp, ea, eb);
   const int64_t tiles = static_cast<int64_t>(g.num_mt) * g.num_nt;
   if (tiles > 0x7fffffff) return QGEMM_ERR_UNSUPPORTED;
-  static bool smem_set[64];
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) return QGEMM_ERR_UNSUPPORTED;
-  if (!smem_set[dev]) {
-    if (cudaFuncSetAttribute(sliced_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kSmem)) != cudaSuccess)
-      return launch_status();
-    smem_set[dev] = true;
+  rc = set_gemm_smem<false>();
+  if (rc) return rc;
+  const int grid = static_cast<int>(std::min<int64_t>(tiles, sm_count()));
+  sliced_gemm_kernel<false><<<grid, kSThreads, kSmem, stream>>>(
+      tmA, tmB, g, nullptr, nullptr, static_cast<int>(tiles), wait_limit_ns());
+  return launch_status();
+}
+
+// ---------------------------------------------------- grouped batches ---
+namespace {
+
+// (op(X))^H = op'(X).
+int op_conjtrans(int op) {
+  switch (op) {
+    case QGEMM_OP_N: return QGEMM_OP_H;
+    case QGEMM_OP_H: return QGEMM_OP_N;
+    case QGEMM_OP_T: return QGEMM_OP_C;
+    default: return QGEMM_OP_T;
   }
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = static_cast<int>(std::min<int64_t>(tiles, sms));
-  sliced_gemm_kernel<<<grid, kSThreads, kSmem, stream>>>(tmA, tmB, g, static_cast<int>(tiles),
-                                                         wait_limit_ns());
+}
+
+// (AB)^H = B^H A^H (Sec. 2.2): a problem is computed as D = op(B)^H op(A)^H
+// and stored as C = conj(D)^T when that pads less (tile rows are padded to
+// 128, columns to 16).
+GemmDesc oriented(const GemmDesc &d, bool *swapped) {
+  auto padded = [](int64_t r, int64_t c) {
+    return ((r + SBM - 1) / SBM) * SBM * (((c + SBNQ - 1) / SBNQ) * SBNQ);
+  };
+  *swapped = d.k > 0 && padded(d.n, d.m) < padded(d.m, d.n);
+  if (!*swapped) return d;
+  GemmDesc t = d;
+  t.m = d.n;
+  t.n = d.m;
+  t.opA = op_conjtrans(d.opB);
+  t.opB = op_conjtrans(d.opA);
+  t.A = d.B;
+  t.B = d.A;
+  return t;
+}
+
+constexpr size_t kGroupedHeader = 256;
+
+struct GroupedLayout {
+  size_t desc_off, tile_off, mtile_off, stile_off, max_off, exp_off, data_off, total;
+  int64_t tiles, mtiles, stiles;
+  std::vector<size_t> maxa, maxb, ea, eb, a_off, b_off;  // per problem, from the workspace
+  std::vector<int64_t> kp;
+  std::vector<GemmDesc> ds;
+  std::vector<int> swapped;
+};
+
+GroupedLayout grouped_layout(const std::vector<GemmDesc> &in) {
+  GroupedLayout L{};
+  const size_t P = in.size();
+  L.ds.resize(P);
+  L.swapped.assign(P, 0);
+  L.maxa.assign(P, 0);
+  L.maxb.assign(P, 0);
+  L.ea.assign(P, 0);
+  L.eb.assign(P, 0);
+  L.a_off.assign(P, 0);
+  L.b_off.assign(P, 0);
+  L.kp.assign(P, 0);
+  size_t maxb_total = 0, exp_total = 0, data = 0;
+  for (size_t p = 0; p < P; ++p) {
+    bool sw = false;
+    L.ds[p] = oriented(in[p], &sw);
+    L.swapped[p] = sw ? 1 : 0;
+    const GemmDesc &d = L.ds[p];
+    L.kp[p] = ((4 * d.k + SBK - 1) / SBK) * SBK;
+    if (d.m == 0 || d.n == 0) continue;
+    L.tiles += ((d.m + SBM - 1) / SBM) * ((d.n + SBNQ - 1) / SBNQ);
+    L.ea[p] = exp_total;
+    L.eb[p] = exp_total + 4 * d.m;
+    exp_total += 4 * (d.m + d.n);
+    if (d.k == 0) continue;
+    L.maxa[p] = maxb_total;
+    L.maxb[p] = maxb_total + 8 * d.m;
+    maxb_total += 8 * (d.m + d.n);
+    L.mtiles += ((d.A.rows + 31) / 32) * ((d.A.cols + 31) / 32) +
+                ((d.B.rows + 31) / 32) * ((d.B.cols + 31) / 32);
+    const int64_t kt = (L.kp[p] / 4 + 31) / 32;
+    L.stiles += ((d.m + 31) / 32) * kt + ((d.n + 31) / 32) * kt;
+    L.a_off[p] = data;
+    data = align_up(data + static_cast<size_t>(NSL) * d.m * L.kp[p] * 2, 1024);
+    L.b_off[p] = data;
+    data = align_up(data + static_cast<size_t>(NSL) * 4 * d.n * L.kp[p] * 2, 1024);
+  }
+  L.desc_off = kGroupedHeader;
+  L.tile_off = align_up(L.desc_off + P * sizeof(SlicedProb), 256);
+  L.mtile_off = align_up(L.tile_off + static_cast<size_t>(L.tiles) * sizeof(int4), 256);
+  L.stile_off = align_up(L.mtile_off + static_cast<size_t>(L.mtiles) * sizeof(int4), 256);
+  L.max_off = align_up(L.stile_off + static_cast<size_t>(L.stiles) * sizeof(int4), 256);
+  L.exp_off = align_up(L.max_off + maxb_total, 256);
+  L.data_off = align_up(L.exp_off + exp_total, 1024);
+  L.total = L.data_off + data;
+  for (size_t p = 0; p < P; ++p) {
+    L.maxa[p] += L.max_off;
+    L.maxb[p] += L.max_off;
+    L.ea[p] += L.exp_off;
+    L.eb[p] += L.exp_off;
+    L.a_off[p] += L.data_off;
+    L.b_off[p] += L.data_off;
+  }
+  return L;
+}
+
+}  // namespace
+
+size_t sliced_grouped_workspace_bytes(const std::vector<GemmDesc> &ds) {
+  return grouped_layout(ds).total;
+}
+
+int prepare_sliced_grouped(const std::vector<GemmDesc> &in, int layout, unsigned char *ws,
+                           size_t ws_bytes, cudaStream_t s, qgemm_grouped_plan *plan) {
+  const GroupedLayout L = grouped_layout(in);
+  if (ws_bytes < L.total) return -6;
+  if (L.tiles > 0x7fffffff || L.mtiles > 0x7fffffff || L.stiles > 0x7fffffff)
+    return QGEMM_ERR_UNSUPPORTED;
+  int rc = set_gemm_smem<true>();
+  if (rc) return rc;
+  std::vector<unsigned char> host(L.max_off - L.desc_off, 0);
+  auto *hd = reinterpret_cast<SlicedProb *>(host.data());
+  std::vector<int4> tiles, mtiles, stiles;
+  std::vector<int> tile_kb;
+  for (size_t p = 0; p < L.ds.size(); ++p) {
+    const GemmDesc &d = L.ds[p];
+    if (d.m == 0 || d.n == 0) continue;
+    SlicedProb &q = hd[p];
+    const int64_t kp = L.kp[p];
+    auto *wa = reinterpret_cast<__nv_bfloat16 *>(ws + L.a_off[p]);
+    auto *wb = reinterpret_cast<__nv_bfloat16 *>(ws + L.b_off[p]);
+    auto *maxa = reinterpret_cast<unsigned long long *>(ws + L.maxa[p]);
+    auto *maxb = reinterpret_cast<unsigned long long *>(ws + L.maxb[p]);
+    int *ea = reinterpret_cast<int *>(ws + L.ea[p]);
+    int *eb = reinterpret_cast<int *>(ws + L.eb[p]);
+    GemmDesc dl = d;
+    dl.layout = layout;
+    q.g = params_for(dl, kp, ea, eb);
+    q.g.swap = L.swapped[p];
+    if (d.k > 0) {
+      const bool bca = max_by_col(false, d.opA), bcb = max_by_col(true, d.opB);
+      q.ma = max_args(d.A, bca, layout, maxa);
+      q.mb = max_args(d.B, bcb, layout, maxb);
+      q.sa = slice_args(false, d.A, d.opA, d.m, d.k, kp, layout, wa, maxa, ea);
+      q.sb = slice_args(true, d.B, d.opB, d.n, d.k, kp, layout, wb, maxb, eb);
+      if (!encode_slices(&q.tmA, wa, kp, d.m, SBM) || !encode_slices(&q.tmB, wb, kp, 4 * d.n, SBN))
+        return QGEMM_ERR_UNSUPPORTED;
+      const MatView *v[2] = {&d.A, &d.B};
+      for (int o = 0; o < 2; ++o)
+        for (int64_t r = 0; r < (v[o]->rows + 31) / 32; ++r)
+          for (int64_t c = 0; c < (v[o]->cols + 31) / 32; ++c)
+            mtiles.push_back(make_int4(static_cast<int>(p), o, static_cast<int>(r),
+                                       static_cast<int>(c)));
+      const int64_t kt = (kp / 4 + 31) / 32;
+      for (int64_t r = 0; r < (d.m + 31) / 32; ++r)
+        for (int64_t c = 0; c < kt; ++c)
+          stiles.push_back(make_int4(static_cast<int>(p), 0, static_cast<int>(r),
+                                     static_cast<int>(c)));
+      for (int64_t r = 0; r < (d.n + 31) / 32; ++r)
+        for (int64_t c = 0; c < kt; ++c)
+          stiles.push_back(make_int4(static_cast<int>(p), 1, static_cast<int>(r),
+                                     static_cast<int>(c)));
+    }
+    for (int a = 0; a < q.g.num_mt; ++a)
+      for (int b = 0; b < q.g.num_nt; ++b) {
+        tiles.push_back(make_int4(static_cast<int>(p), a, b, 0));
+        tile_kb.push_back(q.g.num_kb);
+      }
+  }
+  // longest tiles first; CTAs take tiles t, t + grid, ...
+  std::vector<int32_t> order(tiles.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<int32_t>(i);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t a, int32_t b) { return tile_kb[a] > tile_kb[b]; });
+  int4 *ht = reinterpret_cast<int4 *>(host.data() + (L.tile_off - L.desc_off));
+  for (size_t i = 0; i < order.size(); ++i) ht[i] = tiles[order[i]];
+  std::memcpy(host.data() + (L.mtile_off - L.desc_off), mtiles.data(),
+              mtiles.size() * sizeof(int4));
+  std::memcpy(host.data() + (L.stile_off - L.desc_off), stiles.data(),
+              stiles.size() * sizeof(int4));
+  if (!host.empty() && cudaMemcpyAsync(ws + L.desc_off, host.data(), host.size(),
+                                       cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    cudaGetLastError();
+    return QGEMM_ERR_CUDA;
+  }
+  const int sms = sm_count();
+  plan->workspace_bytes = L.total;
+  plan->tiles = L.tiles;
+  plan->grid = static_cast<int32_t>(std::min<int64_t>(std::max<int64_t>(L.tiles, 1), sms));
+  plan->reserved0 = 8 * sms;  // pre-pass CTAs (grid-stride over the tile lists)
+  plan->desc_offset = static_cast<int64_t>(L.desc_off);
+  plan->tile_offset = static_cast<int64_t>(L.tile_off);
+  plan->data_offset = static_cast<int64_t>(L.max_off);
+  plan->reserved[0] = static_cast<int64_t>(L.mtile_off);
+  plan->reserved[1] = L.mtiles | (L.stiles << 32);
+  plan->reserved[2] = static_cast<int64_t>(L.stile_off);
+  plan->reserved[3] = static_cast<int64_t>(L.exp_off - L.max_off);
+  return QGEMM_SUCCESS;
+}
+
+int launch_sliced_grouped(const qgemm_grouped_plan *plan, cudaStream_t s) {
+  int rc = set_gemm_smem<true>();
+  if (rc) return rc;
+  unsigned char *ws = static_cast<unsigned char *>(plan->workspace);
+  const auto *probs = reinterpret_cast<const SlicedProb *>(ws + plan->desc_offset);
+  const auto *tiles = reinterpret_cast<const int4 *>(ws + plan->tile_offset);
+  const auto *mtiles = reinterpret_cast<const int4 *>(ws + plan->reserved[0]);
+  const auto *stiles = reinterpret_cast<const int4 *>(ws + plan->reserved[2]);
+  const int nm = static_cast<int>(plan->reserved[1] & 0xffffffff);
+  const int ns = static_cast<int>(plan->reserved[1] >> 32);
+  if (plan->reserved[3] > 0 &&
+      cudaMemsetAsync(ws + plan->data_offset, 0, static_cast<size_t>(plan->reserved[3]), s) !=
+          cudaSuccess)
+    return launch_status();
+  const int pgrid = plan->reserved0 > 0 ? plan->reserved0 : 1;
+  if (nm > 0) grouped_slice_max_kernel<<<std::min(nm, pgrid), 256, 0, s>>>(probs, mtiles, nm);
+  if (ns > 0) grouped_slice_kernel<<<std::min(ns, pgrid), 256, 0, s>>>(probs, stiles, ns);
+  CUtensorMap none;
+  std::memset(&none, 0, sizeof(none));
+  const SlicedParams unused{};
+  sliced_gemm_kernel<true><<<plan->grid, kSThreads, kSmem, s>>>(
+      none, none, unused, probs, tiles, static_cast<int>(plan->tiles), wait_limit_ns());
   return launch_status();
 }
 

@@ -23,6 +23,13 @@
 
 namespace qg {
 
+// Digit-sliced FP64 batches (fp64_sliced.cu).
+size_t sliced_grouped_workspace_bytes(const std::vector<GemmDesc> &ds);
+int prepare_sliced_grouped(const std::vector<GemmDesc> &ds, int layout, unsigned char *ws,
+                           size_t ws_bytes, cudaStream_t s, qgemm_grouped_plan *plan);
+int launch_sliced_grouped(const qgemm_grouped_plan *plan, cudaStream_t s);
+
+
 __device__ int g_grouped_error;
 
 fp64::Operands fp64_operands(const GemmDesc &d);
@@ -173,7 +180,7 @@ int validate_problems(const qgemm_problem *problems, int64_t count, int layout, 
   if (count < 0) return -2;
   if (count > 0 && problems == nullptr) return -1;
   if (layout != QGEMM_INTERLEAVED && layout != QGEMM_SPLIT_PLANES) return -3;
-  if (precision != QGEMM_FP64 && precision != QGEMM_FP32_SPLIT_BF16) return -4;
+  if (!precision_ok(precision)) return -4;
   out->resize(static_cast<size_t>(count));
   for (int64_t p = 0; p < count; ++p) {
     const qgemm_problem &q = problems[p];
@@ -667,6 +674,7 @@ size_t qgemm_grouped_workspace_bytes(const qgemm_problem *problems, int64_t coun
   std::vector<GemmDesc> ds;
   if (validate_problems(problems, count, layout, precision, &ds)) return 0;
   if (precision == QGEMM_FP64) return layout_fp64(ds).total;
+  if (precision == QGEMM_FP64_SLICED_BF16) return sliced_grouped_workspace_bytes(ds);
   if (fused_enabled()) {
     std::vector<unsigned char> probe(ds.size() * sizeof(split::FusedProb), 0);
     if (fused_descs(ds, layout, reinterpret_cast<split::FusedProb *>(probe.data())))
@@ -691,6 +699,9 @@ int qgemm_grouped_prepare(const qgemm_problem *problems, int64_t count, int layo
     plan->layout = layout;
     plan->precision = precision;
     plan->count = count;
+    if (precision == QGEMM_FP64_SLICED_BF16)
+      return prepare_sliced_grouped(ds, layout, static_cast<unsigned char *>(workspace),
+                                    workspace_bytes, static_cast<cudaStream_t>(stream), plan);
     if (fused_enabled()) {
       rc = prepare_fused(ds, layout, static_cast<unsigned char *>(workspace), workspace_bytes,
                          static_cast<cudaStream_t>(stream), plan);
@@ -772,6 +783,8 @@ int qgemm_grouped_launch(const qgemm_grouped_plan *plan, void *stream) {
   if (plan->tiles == 0) return QGEMM_SUCCESS;
   int rc = device_ready();
   if (rc) return rc;
+  if (plan->precision == QGEMM_FP64_SLICED_BF16)
+    return launch_sliced_grouped(plan, static_cast<cudaStream_t>(stream));
   if (plan->precision == QGEMM_FP32_SPLIT_BF16)
     return plan->reserved[2] == 1 ? launch_fused(plan, static_cast<cudaStream_t>(stream))
                                   : launch_split(plan, static_cast<cudaStream_t>(stream));

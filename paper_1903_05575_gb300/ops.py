@@ -136,12 +136,13 @@ class GroupedBatch:
     one persistent launch (C ABI qgemm_grouped_prepare / qgemm_grouped_launch).
 
     problems: sequence of dicts with keys opA, opB, m, n, k, alpha, beta, A, B,
-    C (tensors of one dtype and layout).  prepare() runs once (not during
+    C (tensors of one dtype and layout); float64 batches take precision
+    "fp64" (DMMA) or "fp64_sliced".  prepare() runs once (not during
     graph capture); launch() only resets a counter and launches, so it can be
     captured in a CUDA graph and replayed.  The tensors must stay alive.
     """
 
-    def __init__(self, problems, layout="interleaved", ws=None, stream=None):
+    def __init__(self, problems, layout="interleaved", ws=None, stream=None, precision=None):
         import ctypes
 
         from . import autotune
@@ -150,7 +151,7 @@ class GroupedBatch:
         if not self.problems:
             raise ValueError("empty batch")
         self.layout = layout
-        self.prec = precision_of(self.problems[0]["C"].dtype)
+        self.prec = precision_of(self.problems[0]["C"].dtype, precision)
         arr = (_abi.QgemmProblem * len(self.problems))()
         for i, p in enumerate(self.problems):
             q = arr[i]

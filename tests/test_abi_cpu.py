@@ -119,3 +119,31 @@ def test_status_strings():
     L = _abi.lib()
     for rc in (0, 1, 2, 3, 4, 5, -3):
         assert len(L.qgemm_status_string(rc)) > 0
+
+
+def test_grouped_workspace_by_precision():
+    """Host-side grouped schedule sizes: the digit-sliced batch needs the
+    six-slice operands (A' 6 x m x kp and B' 6 x 4n x kp BF16) on top of its
+    descriptors; an unknown precision gives 0 (invalid)."""
+    L = _abi.lib()
+    arr = (_abi.QgemmProblem * 2)()
+    for i, (m, n, k) in enumerate(((100, 30, 50), (20, 200, 7))):
+        q = arr[i]
+        q.opA = q.opB = 0
+        q.m, q.n, q.k = m, n, k
+        q.alpha[0] = 1.0
+        q.A = q.B = q.C = 64
+        q.lda, q.ldb, q.ldc = m, k, m
+    sizes = {p: L.qgemm_grouped_workspace_bytes(arr, 2, 0, p) for p in (0, 1, 2, 3)}
+    slices = 0
+    for (m, n, k) in ((100, 30, 50), (20, 200, 7)):
+        kp = (4 * k + 31) // 32 * 32
+
+        def padded(r, c):   # tiles of 128 rows x 16 quaternion columns
+            return -(-r // 128) * 128 * (-(-c // 16) * 16)
+        if padded(n, m) < padded(m, n):   # computed as (AB)^H = B^H A^H
+            m, n = n, m
+        slices += 6 * 2 * kp * (m + 4 * n)
+    assert sizes[2] >= slices
+    assert sizes[0] > 0 and sizes[1] > 0
+    assert sizes[3] == 0

@@ -252,3 +252,68 @@ def test_fp64_batch_mixing_tma_and_plain_load_problems():
         check_batch(host, dev, "planes", 1e-12)
     finally:
         set_tile_table(None)
+
+
+# ------------------------------------------------ digit-sliced FP64 batches
+@pytest.mark.parametrize("layout", qsynth.LAYOUTS)
+def test_sliced_mixed_batch(layout):
+    """Every op pair, ragged sizes (row tiles of 128, column tiles of 16,
+    several 256-k chunks), both orientations of the (AB)^H = B^H A^H swap."""
+    g = qsynth.rng(15)
+    specs = []
+    for i in range(48):
+        m, n, k = (int(x) for x in g.integers(1, 200, size=3))
+        if i % 3 == 0:
+            m, n = n // 8 + 1, m      # wide problems: computed transposed
+        specs.append((OPS[i % 4], OPS[(i // 4) % 4], m, n, k))
+    host, dev = make_batch(specs, layout, seed=1100)
+    b = GroupedBatch(dev, layout=layout, precision="fp64_sliced")
+    b.launch()
+    torch.cuda.synchronize()
+    worst = check_batch(host, dev, layout, 1e-12)
+    print("sliced mixed batch worst rel err %.3e" % worst)
+    assert _abi.lib().qgemm_get_last_device_error() == 0
+
+
+def test_sliced_zero_sized_and_scale_only_problems():
+    specs = [("N", "N", 20, 30, 0), ("N", "N", 16, 16, 16), ("H", "N", 0, 5, 7),
+             ("N", "H", 33, 17, 300)]
+    host, dev = make_batch(specs, "interleaved", seed=1300)
+    host[1]["alpha"] = np.zeros(4)
+    dev[1]["alpha"] = np.zeros(4)
+    b = GroupedBatch(dev, precision="fp64_sliced")
+    b.launch()
+    torch.cuda.synchronize()
+    check_batch(host, dev, "interleaved", 1e-12)
+
+
+def test_sliced_graph_replay():
+    specs = [("N", "H", 150, 40, 300), ("H", "N", 20, 64, 48), ("N", "N", 33, 133, 33)]
+    host, dev = make_batch(specs, "interleaved", seed=1600)
+    b = GroupedBatch(dev, precision="fp64_sliced")
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    C0 = [d["C"].clone() for d in dev]
+    with torch.cuda.graph(g, stream=stream):
+        b.launch(stream=stream)
+    for _ in range(2):
+        for d, c0 in zip(dev, C0):
+            d["C"].copy_(c0)
+        g.replay()
+        torch.cuda.synchronize()
+        check_batch(host, dev, "interleaved", 1e-12)
+
+
+def test_config4_sliced_batch_sampled():
+    """4096 problems, m, n, k iid uniform in [8, 256], ops iid in {N, H},
+    FP64 data on the digit-sliced path."""
+    probs = qsynth.grouped_problems(4096, 1907)
+    specs = [(p["opA"], p["opB"], p["m"], p["n"], p["k"]) for p in probs]
+    host, dev = make_batch(specs, "interleaved", seed=500, pad=0)
+    b = GroupedBatch(dev, precision="fp64_sliced")
+    b.launch()
+    torch.cuda.synchronize()
+    worst = check_batch(host, dev, "interleaved", 1e-12, full=False)
+    print("config4 sliced worst sampled rel err %.3e" % worst)
+    assert _abi.lib().qgemm_get_last_device_error() == 0

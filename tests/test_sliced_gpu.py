@@ -237,3 +237,13 @@ def test_2048_sampled_and_status():
     print("2048 sliced sampled rel err %.3e" % err)
     assert err <= TOL
     assert ops.last_device_error() == 0
+
+
+@pytest.mark.parametrize("scalars", [((2.0, 0, 0, 0), (-0.5, 0, 0, 0)),
+                                     ((1.0, 0, 0, 0), (0.25, 1.0, 0, 0)),
+                                     ((0.5, 0.5, -0.5, 0.5), (3.0, 0, 0, 0))])
+def test_real_and_quaternion_scalars(scalars):
+    """Real alpha or beta take the 4-product epilogue, quaternion ones the
+    16-product Hamilton form; both against the oracle."""
+    al, be = (np.array(x) for x in scalars)
+    check("N", "H", 140, 33, 90, "interleaved", seed=901, alpha=al, beta=be)
