@@ -63,6 +63,10 @@ def _bind(path):
     lib.oracle_qherk.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, ctypes.c_double, dp, i64,
                                  i64, ctypes.c_double, dp, i64, i64, ctypes.c_int, ctypes.c_int]
     lib.oracle_qherk.restype = ctypes.c_int
+    lib.oracle_qtrmm.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, i64,
+                                 dp, dp, i64, i64, dp, i64, i64, dp, i64, i64, ctypes.c_int,
+                                 ctypes.c_int]
+    lib.oracle_qtrmm.restype = ctypes.c_int
     lib.oracle_max_threads.argtypes = []
     lib.oracle_max_threads.restype = ctypes.c_int
     return lib
@@ -169,4 +173,24 @@ def qherk(uplo, trans, n, k, alpha, A, beta, C, layout="interleaved", nthreads=0
                           psA, float(beta), _dptr(C), ldc, psC, LAYOUTS[layout], int(nthreads))
     if rc != 0:
         raise ValueError("oracle_qherk returned %d" % rc)
+    return C
+
+
+def qtrmm(side, uplo, trans, diag, m, n, alpha, A, B, C, layout="interleaved", nthreads=0,
+          lib=None):
+    """Triangular product into C (written, not read): side L: C = alpha op(tri(A)) B,
+    side R: C = alpha B op(tri(A)); tri(A) = the uplo triangle of A, unit
+    diagonal when diag is "U"."""
+    lib = lib or _load()
+    for X in (A, B, C):
+        _check(X)
+    lda, psA, _ = geometry(A, layout)
+    ldb, psB, _ = geometry(B, layout)
+    ldc, psC, _ = geometry(C, layout)
+    al = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64).reshape(4))
+    rc = lib.oracle_qtrmm({"L": 0, "R": 1}[side], {"L": 0, "U": 1}[uplo], OPS[trans],
+                          {"N": 0, "U": 1}[diag], m, n, _dptr(al), _dptr(A), lda, psA, _dptr(B),
+                          ldb, psB, _dptr(C), ldc, psC, LAYOUTS[layout], int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_qtrmm returned %d" % rc)
     return C

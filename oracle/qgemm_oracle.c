@@ -302,6 +302,82 @@ int oracle_qherk(int uplo, int trans, int64_t n, int64_t k, double alpha,
     return 0;
 }
 
+/*
+ * Triangular matrix product, out of place (the XTRMM of the BLAS-3 set that
+ * Sec. 3 builds on the GEMM kernels):
+ *   side 0 (left):  C <- alpha op(T) B,   T = tri(A), m x m,  B and C m x n
+ *   side 1 (right): C <- alpha B op(T),   T = tri(A), n x n
+ * tri(A) is the stored triangle of A (uplo 0: lower, r >= c; 1: upper,
+ * r <= c) with zeros elsewhere; diag 1 (unit) takes the diagonal as the
+ * quaternion 1 and does not read it.  op as in oracle_qgemm; alpha
+ * multiplies from the left.  C is written, not read.
+ */
+static void load_tri(const double *A, int64_t lda, int64_t psA, int layout, int uplo, int diag,
+                     int64_t r, int64_t c, double q[4])
+{
+    if (diag && r == c) {
+        q[0] = 1.0; q[1] = q[2] = q[3] = 0.0;
+        return;
+    }
+    const int in_triangle = uplo == 0 ? r >= c : r <= c;
+    if (!in_triangle) {
+        q[0] = q[1] = q[2] = q[3] = 0.0;
+        return;
+    }
+    load_stored(A, lda, psA, layout, r, c, q);
+}
+
+/* op(T)_{r c} for T = tri(A). */
+static void load_op_tri(const double *A, int64_t lda, int64_t psA, int layout, int uplo,
+                        int diag, int op, int64_t r, int64_t c, double q[4])
+{
+    if (op == ORACLE_OP_T || op == ORACLE_OP_H)
+        load_tri(A, lda, psA, layout, uplo, diag, c, r, q);
+    else
+        load_tri(A, lda, psA, layout, uplo, diag, r, c, q);
+    if (op == ORACLE_OP_C || op == ORACLE_OP_H) conjugate(q);
+}
+
+int oracle_qtrmm(int side, int uplo, int trans, int diag, int64_t m, int64_t n,
+                 const double alpha[4], const double *A, int64_t lda, int64_t psA,
+                 const double *B, int64_t ldb, int64_t psB, double *C, int64_t ldc, int64_t psC,
+                 int layout, int nthreads)
+{
+    if (m < 0 || n < 0) return -1;
+    if ((side != 0 && side != 1) || (uplo != 0 && uplo != 1) || (diag != 0 && diag != 1))
+        return -1;
+    if (trans < ORACLE_OP_N || trans > ORACLE_OP_H) return -1;
+    if (layout != ORACLE_INTERLEAVED && layout != ORACLE_SPLIT_PLANES) return -1;
+    const int64_t kdim = side == 0 ? m : n;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t j = 0; j < n; ++j) {
+        for (int64_t i = 0; i < m; ++i) {
+            double P[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int64_t kap = 0; kap < kdim; ++kap) {
+                double a[4], b[4], ab[4];
+                if (side == 0) {
+                    load_op_tri(A, lda, psA, layout, uplo, diag, trans, i, kap, a);
+                    load_stored(B, ldb, psB, layout, kap, j, b);
+                } else {
+                    load_stored(B, ldb, psB, layout, i, kap, a);
+                    load_op_tri(A, lda, psA, layout, uplo, diag, trans, kap, j, b);
+                }
+                oracle_hamilton(a, b, ab);
+                P[0] += ab[0]; P[1] += ab[1]; P[2] += ab[2]; P[3] += ab[3];
+            }
+            double out[4];
+            oracle_hamilton(alpha, P, out);
+            store_stored(C, ldc, psC, layout, i, j, out);
+        }
+    }
+    return 0;
+}
+
 /* Number of OpenMP threads the oracle would use by default. */
 int oracle_max_threads(void)
 {

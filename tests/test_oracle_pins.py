@@ -289,10 +289,77 @@ def pin_herk_vs_complex(lib):
     return True
 
 
+def _tri_components(Ac, uplo, diag):
+    """tri(A) on a (K, K, 4) component array: the uplo triangle, zeros
+    elsewhere, the quaternion 1 on the diagonal when diag is "U"."""
+    K = Ac.shape[0]
+    mask = np.tril(np.ones((K, K), bool)) if uplo == "L" else np.triu(np.ones((K, K), bool))
+    T = Ac * mask[:, :, None]
+    if diag == "U":
+        T[np.arange(K), np.arange(K)] = np.array([1.0, 0.0, 0.0, 0.0])
+    return T
+
+
+def pin_trmm_vs_complex(lib):
+    """Triangular product (the BLAS-3 XTRMM built on GEMM, Sec. 3): C equals
+    alpha op(tri(A)) B (left) or alpha B op(tri(A)) (right) computed through
+    the complex representation (numpy), exactly on small integers, for every
+    side, triangle, op and diagonal kind."""
+    m, n = 4, 3
+    alpha = np.array([2.0, -1.0, 1.0, 3.0])
+    for layout in qsynth.LAYOUTS:
+        for side in ("L", "R"):
+            K = m if side == "L" else n
+            A = qsynth.small_int(K, K, 93, layout, ld=K + 1)
+            B = qsynth.small_int(m, n, 94, layout, ld=m + 2)
+            Ac = qsynth.components(A, K, layout)
+            Bc = qsynth.components(B, m, layout)
+            for uplo in ("L", "U"):
+                for trans in "NTCH":
+                    for diag in ("N", "U"):
+                        got = qsynth.empty(m, n, layout, ld=m + 1)
+                        orc.qtrmm(side, uplo, trans, diag, m, n, alpha, A, B, got,
+                                  layout=layout, lib=lib)
+                        T = qref.apply_op(_tri_components(Ac, uplo, diag), trans)
+                        P = (qref.to_complex(T) @ qref.to_complex(Bc) if side == "L"
+                             else qref.to_complex(Bc) @ qref.to_complex(T))
+                        want = qref.from_complex(np.kron(qref.scalar_complex(alpha), np.eye(m)) @ P,
+                                                 m, n)
+                        if not np.array_equal(qsynth.components(got, m, layout), want):
+                            return False
+    return True
+
+
+def pin_trmm_transpose_duality(lib):
+    """op(tri(A)) with op T is tri of the transposed matrix in the other
+    triangle: qtrmm(uplo, T, A) = qtrmm(other uplo, N, A^T stored), and with
+    op H the same on the conjugate transpose; a unit triangle of zeros gives
+    C = alpha B."""
+    m, n = 5, 4
+    alpha = np.array([1.0, 2.0, 0.0, -1.0])
+    A = qsynth.small_int(m, m, 95)
+    B = qsynth.small_int(m, n, 96)
+    Ac = qsynth.components(A, m, "interleaved")
+    for uplo, other in (("L", "U"), ("U", "L")):
+        for trans, flip in (("T", np.array([1.0, 1.0, 1.0, 1.0])),
+                            ("H", np.array([1.0, -1.0, -1.0, -1.0]))):
+            At = qsynth.empty(m, m)
+            At[:, :m, :] = np.transpose(np.transpose(Ac, (1, 0, 2)) * flip, (1, 0, 2))
+            x = orc.qtrmm("L", uplo, trans, "N", m, n, alpha, A, B, qsynth.empty(m, n), lib=lib)
+            y = orc.qtrmm("L", other, "N", "N", m, n, alpha, At, B, qsynth.empty(m, n), lib=lib)
+            if not np.array_equal(x, y):
+                return False
+    Z = qsynth.empty(m, m, pad=0.0)
+    got = orc.qtrmm("L", "L", "N", "U", m, n, alpha, Z, B, qsynth.empty(m, n), lib=lib)
+    Bc = qsynth.components(B, m, "interleaved")
+    want = np.array([[orc.hamilton(alpha, Bc[i, j], lib=lib) for j in range(n)] for i in range(m)])
+    return np.array_equal(qsynth.components(got, m, "interleaved"), want)
+
+
 PINS = [pin_basis_table, pin_worked_products, pin_norm_multiplicative, pin_complex_subalgebra,
         pin_scalar_complex_rep, pin_gemm_vs_complex, pin_conj_transpose_identity,
         pin_associative, pin_scalar_side, pin_blas_conventions, pin_entries_match_full,
-        pin_herk_vs_complex]
+        pin_herk_vs_complex, pin_trmm_vs_complex, pin_trmm_transpose_duality]
 
 
 def failing_pins(lib, pins=PINS):
@@ -349,6 +416,14 @@ MUTATIONS = {
     "herk_diag_not_real": ("if (i == j) out[1] = out[2] = out[3] = 0.0;", "(void)0;"),
     "herk_operands_swapped": ("load_op(A, lda, psA, layout, trans, i, kap, a);\n                load_op(A, lda, psA, layout, trans, j, kap, b);",
                               "load_op(A, lda, psA, layout, trans, j, kap, a);\n                load_op(A, lda, psA, layout, trans, i, kap, b);"),
+    "trmm_triangle_flipped": ("const int in_triangle = uplo == 0 ? r >= c : r <= c;",
+                              "const int in_triangle = uplo == 0 ? r <= c : r >= c;"),
+    "trmm_unit_diag_ignored": ("    if (diag && r == c) {\n        q[0] = 1.0;",
+                               "    if (0 && r == c) {\n        q[0] = 1.0;"),
+    "trmm_transpose_before_mask": ("        load_tri(A, lda, psA, layout, uplo, diag, c, r, q);",
+                                   "        load_stored(A, lda, psA, layout, c, r, q);"),
+    "trmm_right_side_order": ("                    load_stored(B, ldb, psB, layout, i, kap, a);\n                    load_op_tri(A, lda, psA, layout, uplo, diag, trans, kap, j, b);",
+                              "                    load_stored(B, ldb, psB, layout, i, kap, b);\n                    load_op_tri(A, lda, psA, layout, uplo, diag, trans, kap, j, a);"),
     "plane_stride_wrong": ("q[0] = e[0]; q[1] = e[ps]; q[2] = e[2 * ps]; q[3] = e[3 * ps];",
                            "q[0] = e[0]; q[1] = e[ps]; q[2] = e[3 * ps]; q[3] = e[2 * ps];"),
 }
