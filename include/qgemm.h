@@ -96,6 +96,12 @@ extern "C" {
 #define QGEMM_LOWER 0
 #define QGEMM_UPPER 1
 
+#define QGEMM_LEFT 0
+#define QGEMM_RIGHT 1
+
+#define QGEMM_NON_UNIT 0
+#define QGEMM_UNIT 1
+
 #define QGEMM_FP64 0
 #define QGEMM_FP32_SPLIT_BF16 1
 #define QGEMM_FP64_SLICED_BF16 2
@@ -280,6 +286,36 @@ int qherk(int uplo, int trans, int64_t n, int64_t k, double alpha,
 
 /* Workspace qherk() needs (0 for QGEMM_FP64). */
 size_t qherk_workspace_bytes(int uplo, int trans, int64_t n, int64_t k,
+                             int layout, int precision);
+
+/*
+ * qtrmm: triangular matrix product, out of place (the quaternion xTRMM; the
+ * paper notes its GEMM kernels also serve triangular products, Sec. 3):
+ *     side = QGEMM_LEFT:   C <- alpha op(T) B     (T m x m, B and C m x n)
+ *     side = QGEMM_RIGHT:  C <- alpha B op(T)     (T n x n)
+ * T = tri(A): the triangle `uplo` of the stored A (QGEMM_LOWER: row >=
+ * column; QGEMM_UPPER: row <= column), zeros elsewhere; diag QGEMM_UNIT takes
+ * the diagonal as the quaternion 1 without reading it.  op(T) as in qgemm();
+ * alpha multiplies from the left.  C is written, not read, and must not
+ * overlap B (C == B is rejected).  The triangle is copied densely into the
+ * workspace and the product runs on the qgemm() kernels of the chosen
+ * precision, each output tile summing only over the k-range where op(T) can
+ * be nonzero.  Arguments, in order for the -i return:
+ *   1 side, 2 uplo, 3 transA, 4 diag, 5 m, 6 n, 7 alpha (host double[4]),
+ *   8 A, 9 lda (>= max(1, m or n)), 10 psA, 11 B, 12 ldb, 13 psB, 14 C,
+ *   15 ldc, 16 psC, 17 layout, 18 precision, 19 workspace, 20 workspace_bytes,
+ *   21 stream.  A workspace is always needed (qtrmm_workspace_bytes()).
+ */
+int qtrmm(int side, int uplo, int transA, int diag, int64_t m, int64_t n,
+          const double alpha[4],
+          const void *A, int64_t lda, int64_t psA,
+          const void *B, int64_t ldb, int64_t psB,
+          void *C, int64_t ldc, int64_t psC,
+          int layout, int precision,
+          void *workspace, size_t workspace_bytes, void *stream);
+
+/* Workspace qtrmm() needs (0 for invalid arguments or an empty C). */
+size_t qtrmm_workspace_bytes(int side, int uplo, int transA, int diag, int64_t m, int64_t n,
                              int layout, int precision);
 
 /*

@@ -200,6 +200,7 @@ fp64::Operands fp64_operands(const GemmDesc &d) {
   a.negmask = block_neg_mask(op_conj(d.opA), op_conj(d.opB));
   a.beta_zero = d.beta_zero ? 1 : 0;
   a.tri = d.tri;
+  a.krange = d.krange;
   return a;
 }
 

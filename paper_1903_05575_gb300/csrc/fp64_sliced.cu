@@ -80,6 +80,7 @@ struct SlicedParams {
   int layout, beta_zero, tri, c_vec2;
   int swap;       // 1: the kernel computes D = (op(A) op(B))^H; store C = conj(D)^T
   int alpha_real, beta_real;  // scalars with zero vector part: 4 FP64 products, not 16
+  int krange;     // k-range of a tile when op(A) or op(B) is triangular (GemmDesc)
   double *C;
   int64_t ldc, psC;
   double alpha[4], beta[4];
@@ -153,6 +154,29 @@ __device__ __forceinline__ void tile_coords(const SlicedParams &g, int t, int &m
   const int gsize = min(g.num_mt - first_m, kGroupM);
   mt = first_m + (t % per_group) % gsize;
   nt = (t % per_group) / gsize;
+  // a triangular operand: the tiles with the longest k-range first, so the
+  // CTAs' round-robin shares stay balanced
+  if (g.krange == 1) mt = g.num_mt - 1 - mt;
+  if (g.krange == 4) nt = g.num_nt - 1 - nt;
+}
+
+// k-blocks [lo, hi) of tile (mt, nt): all of K, or the part where a
+// triangular operand can be nonzero for the tile's rows or columns.
+__device__ __forceinline__ void kb_range(const SlicedParams &g, int mt, int nt, int &lo, int &hi) {
+  lo = 0;
+  hi = g.num_kb;
+  const int64_t rq0 = static_cast<int64_t>(mt) * SBM, cq0 = static_cast<int64_t>(nt) * SBNQ;
+  if (g.krange == 1) {
+    const int64_t e = (4 * (rq0 + SBM) + SBK - 1) / SBK;
+    if (e < hi) hi = static_cast<int>(e);
+  }
+  if (g.krange == 2) lo = static_cast<int>(4 * rq0 / SBK);
+  if (g.krange == 3) lo = static_cast<int>(4 * cq0 / SBK);
+  if (g.krange == 4) {
+    const int64_t e = (4 * (cq0 + SBNQ) + SBK - 1) / SBK;
+    if (e < hi) hi = static_cast<int>(e);
+  }
+  if (lo > hi) lo = hi;
 }
 
 __device__ __forceinline__ bool tile_skip(const SlicedParams &g, int mt, int nt) {
@@ -426,8 +450,9 @@ __global__ void __launch_bounds__(kSThreads, 1)
         int mt, nt;
         tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt);
         if (tile_skip(*g, mt, nt)) continue;
-        const int nkb = g->num_kb;
-        for (int kb = 0; kb < nkb; ++kb, ++s_run) {
+        int kb_lo, kb_hi;
+        kb_range(*g, mt, nt, kb_lo, kb_hi);
+        for (int kb = kb_lo; kb < kb_hi; ++kb, ++s_run) {
           const int st = s_run % SST;
           if (!wait_phase(&ctl->empty[st], ((s_run / SST) & 1) ^ 1, limit_ns, ctl)) {
             set_abort(ctl);
@@ -460,8 +485,9 @@ __global__ void __launch_bounds__(kSThreads, 1)
         int mt, nt;
         tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt);
         if (tile_skip(*g, mt, nt)) continue;
-        const int nkb = g->num_kb;
-        const int nch = (nkb + kChunkKb - 1) / kChunkKb;
+        int kb_lo, kb_hi;
+        kb_range(*g, mt, nt, kb_lo, kb_hi);
+        const int nch = (kb_hi - kb_lo + kChunkKb - 1) / kChunkKb;
         for (int ch = 0; ch < nch && ok; ++ch, ++c_run) {
           const uint32_t par = (c_run & 1) ^ 1;
           if (!wait_phase(&ctl->free23, par, limit_ns, ctl)) {
@@ -470,7 +496,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
             break;
           }
           tc_fence_after();
-          const int kb0 = ch * kChunkKb, kb1 = min(nkb, kb0 + kChunkKb);
+          const int kb0 = kb_lo + ch * kChunkKb, kb1 = min(kb_hi, kb0 + kChunkKb);
           for (int kb = kb0; kb < kb1; ++kb, ++s_run) {
             const int st = s_run % SST;
             if (!wait_phase(&ctl->full[st], (s_run / SST) & 1, limit_ns, ctl)) {
@@ -530,7 +556,9 @@ __global__ void __launch_bounds__(kSThreads, 1)
       int mt, nt;
       tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt);
       if (tile_skip(*g, mt, nt)) continue;
-      const int nch = (g->num_kb + kChunkKb - 1) / kChunkKb;
+      int kb_lo, kb_hi;
+      kb_range(*g, mt, nt, kb_lo, kb_hi);
+      const int nch = (kb_hi - kb_lo + kChunkKb - 1) / kChunkKb;
       const int nbound = nch - 1;  // chunk ends before the tile's last
       long long T[32];
 #pragma unroll
@@ -968,6 +996,7 @@ SlicedParams params_for(const GemmDesc &d, int64_t kp, const int *ea, const int 
   g.swap = 0;
   g.alpha_real = (d.alpha[1] == 0.0 && d.alpha[2] == 0.0 && d.alpha[3] == 0.0) ? 1 : 0;
   g.beta_real = (d.beta[1] == 0.0 && d.beta[2] == 0.0 && d.beta[3] == 0.0) ? 1 : 0;
+  g.krange = d.krange;
   g.c_vec2 = (reinterpret_cast<uintptr_t>(d.C) % 16 == 0) ? 1 : 0;
   g.C = static_cast<double *>(d.C);
   g.ldc = d.ldc;

@@ -42,6 +42,7 @@ struct Operands {
   uint32_t negmask;
   int tmaA, tmaB, beta_zero;
   int tri;  // 0 full; 1 lower (row >= col) only; 2 upper; diagonal written real
+  int krange;  // k-range of a tile when op(A) or op(B) is triangular (see GemmDesc)
 };
 
 // True when the tile at quaternion offset (i0, n0) of size BMQ x BNQ has no
@@ -121,7 +122,14 @@ __device__ bool tile(const Operands &p, const CUtensorMap *tmA, const CUtensorMa
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int wm = warp % WARPS_M, wn = warp / WARPS_M;
-  const int ktiles = static_cast<int>((p.k + kBKQ - 1) / kBKQ);
+  // k-blocks [kt_lo, kt_lo + ktiles): all of K, or the part where a
+  // triangular operand can be nonzero for this tile's rows or columns
+  int kt_lo = 0, kt_hi = static_cast<int>((p.k + kBKQ - 1) / kBKQ);
+  if (p.krange == 1) kt_hi = min(kt_hi, static_cast<int>((i0 + BMQ + kBKQ - 1) / kBKQ));
+  if (p.krange == 2) kt_lo = static_cast<int>(i0 / kBKQ);
+  if (p.krange == 3) kt_lo = static_cast<int>(n0 / kBKQ);
+  if (p.krange == 4) kt_hi = min(kt_hi, static_cast<int>((n0 + BNQ + kBKQ - 1) / kBKQ));
+  const int ktiles = kt_hi > kt_lo ? kt_hi - kt_lo : 0;
   const uint32_t tx_bytes = (p.tmaA ? kABytes : 0u) + (p.tmaB ? kBBytes : 0u);
 
   // Every k-block arrives on its ring slot's barrier, with the TMA byte count
@@ -132,7 +140,7 @@ __device__ bool tile(const Operands &p, const CUtensorMap *tmA, const CUtensorMa
     const uint32_t q = kb_run + kt;
     const int st = q % kStages;
     mbar_arrive_expect_tx(&full[st], tx_bytes);
-    const int64_t kk0 = static_cast<int64_t>(kt) * kBKQ;
+    const int64_t kk0 = static_cast<int64_t>(kt_lo + kt) * kBKQ;
     if (p.tmaA) tma_box(sA + st * kMaxTileElems, tmA, &full[st], LAYOUT, TA ? kk0 : i0, TA ? i0 : kk0);
     if (p.tmaB) tma_box(sB + st * kMaxTileElems, tmB, &full[st], LAYOUT, TB ? n0 : kk0, TB ? kk0 : n0);
   };
@@ -166,7 +174,7 @@ __device__ bool tile(const Operands &p, const CUtensorMap *tmA, const CUtensorMa
     const uint32_t q = kb_run + kt;
     const int st = q % kStages;
     const uint32_t par = (q / kStages) & 1;
-    const int64_t kk0 = static_cast<int64_t>(kt) * kBKQ;
+    const int64_t kk0 = static_cast<int64_t>(kt_lo + kt) * kBKQ;
     double *a_t = sA + st * kMaxTileElems;
     double *b_t = sB + st * kMaxTileElems;
     if (!p.tmaA)

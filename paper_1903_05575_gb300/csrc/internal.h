@@ -30,6 +30,10 @@ struct GemmDesc {
   int layout;
   bool beta_zero;
   int tri;  // 0: full C; 1: lower triangle only; 2: upper (Hermitian rank-k update)
+  // k-range of an output tile when one operand is triangular (qtrmm): 0 all
+  // of K; 1 kappa < tile row end; 2 kappa >= tile row start; 3 kappa >= tile
+  // column start; 4 kappa < tile column end.
+  int krange;
 };
 
 inline bool op_trans(int op) { return op == QGEMM_OP_T || op == QGEMM_OP_H; }

@@ -111,6 +111,7 @@ GemmParams gemm_params(const GemmDesc &d, int64_t kp) {
   g.layout = d.layout;
   g.beta_zero = d.beta_zero ? 1 : 0;
   g.tri = d.tri;
+  g.krange = d.krange;
   g.c_vec4 = (reinterpret_cast<uintptr_t>(d.C) % 16 == 0) ? 1 : 0;
   for (int s = 0; s < 4; ++s) {
     g.alpha[s] = static_cast<float>(d.alpha[s]);

@@ -255,7 +255,27 @@ struct GemmParams {
   float alpha[4], beta[4];
   int tri;                // 0 full; 1 lower (row >= col) only; 2 upper; real diagonal
   int swap;               // 1: the kernel computed D = (op(A) op(B))^H; store C = conj(D)^T
+  int krange;             // k-range of a tile when op(A) or op(B) is triangular (GemmDesc)
 };
+
+// k-blocks [lo, hi) of tile (mt, nt): all of K, or the part where a
+// triangular operand can be nonzero for the tile's rows or columns.
+__host__ __device__ inline void kb_range(const GemmParams &g, int mt, int nt, int &lo, int &hi) {
+  lo = 0;
+  hi = g.num_kb;
+  const int64_t rq0 = static_cast<int64_t>(mt) * BM, cq0 = static_cast<int64_t>(nt) * BNQ;
+  if (g.krange == 1) {
+    const int64_t e = (4 * (rq0 + BM) + BK - 1) / BK;
+    if (e < hi) hi = static_cast<int>(e);
+  }
+  if (g.krange == 2) lo = static_cast<int>(4 * rq0 / BK);
+  if (g.krange == 3) lo = static_cast<int>(4 * cq0 / BK);
+  if (g.krange == 4) {
+    const int64_t e = (4 * (cq0 + BNQ) + BK - 1) / BK;
+    if (e < hi) hi = static_cast<int>(e);
+  }
+  if (lo > hi) lo = hi;
+}
 
 // Device descriptor of one problem of a grouped batch.
 struct alignas(128) SplitProb {
@@ -325,6 +345,10 @@ __device__ __forceinline__ void tile_of(int t, const GemmParams &single, const C
     const int gsize = min(single.num_mt - first_m, kGroupM);
     mt = first_m + (t % per_group) % gsize;
     nt = (t % per_group) / gsize;
+    // a triangular operand: the tiles with the longest k-range first, so the
+    // CTAs' round-robin shares stay balanced
+    if (single.krange == 1) mt = single.num_mt - 1 - mt;
+    if (single.krange == 4) nt = single.num_nt - 1 - nt;
   }
 }
 
@@ -454,8 +478,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         int mt, nt;
         tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt);
         if (tile_skip(*g, mt, nt)) continue;
-        const int nkb = g->num_kb;
-        for (int kb = 0; kb < nkb; ++kb, ++s_run) {
+        int kb_lo, kb_hi;
+        kb_range(*g, mt, nt, kb_lo, kb_hi);
+        for (int kb = kb_lo; kb < kb_hi; ++kb, ++s_run) {
           const int st = s_run % STAGES;
           if (!wait_phase(&ctl->empty[st], ((s_run / STAGES) & 1) ^ 1, limit_ns, ctl)) {
             set_abort<Err>(ctl);
@@ -486,8 +511,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         int mt, nt;
         tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt);
         if (tile_skip(*g, mt, nt)) continue;
-        const int nkb = g->num_kb;
-        for (int kb = 0; kb < nkb && ok; ++c_run) {
+        int kb_lo, nkb;
+        kb_range(*g, mt, nt, kb_lo, nkb);
+        for (int kb = kb_lo; kb < nkb && ok; ++c_run) {
           const int b = c_run & 1;
           if (!wait_phase(&ctl->accempty[b], ((c_run >> 1) & 1) ^ 1, limit_ns, ctl)) {
             set_abort<Err>(ctl);
@@ -542,8 +568,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       int mt, nt;
       tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt);
       if (tile_skip(*g, mt, nt)) continue;
-      const int nkb = g->num_kb;
-      const int nch = (nkb + chunk - 1) / chunk;
+      int kb_lo, kb_hi;
+      kb_range(*g, mt, nt, kb_lo, kb_hi);
+      const int nch = (kb_hi - kb_lo + chunk - 1) / chunk;
       float acc[128];
 #pragma unroll
       for (int i = 0; i < 128; ++i) acc[i] = 0.f;
@@ -749,6 +776,10 @@ __device__ __forceinline__ void fused_tile_of(int t, const GemmParams &single,
     const int gsize = min(single.num_mt - first_m, kGroupM);
     mt = first_m + (t % per_group) % gsize;
     nt = (t % per_group) / gsize;
+    // a triangular operand: the tiles with the longest k-range first, so the
+    // CTAs' round-robin shares stay balanced
+    if (single.krange == 1) mt = single.num_mt - 1 - mt;
+    if (single.krange == 4) nt = single.num_nt - 1 - nt;
   }
 }
 
@@ -890,7 +921,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         fused_tile_of<GROUPED>(t, single, single_o, &tmA, &tmB, probs, tiles, g, o, mA, mB, mt,
                                nt);
         if (tile_skip(*g, mt, nt)) continue;
-        const int nkb = g->num_kb;
+        const int nkb = g->num_kb;  // the fused path runs all of K
         for (int kb = 0; kb < nkb && ok; ++c_run) {
           const int b = c_run & 1;
           if (!fused_wait(&ctl->accempty[b], ((c_run >> 1) & 1) ^ 1, limit_ns, ctl)) {

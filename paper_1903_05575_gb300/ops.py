@@ -106,6 +106,32 @@ def qherk(uplo, trans, n, k, alpha, A, beta, C, layout="interleaved", ws=None, s
     return C
 
 
+def qtrmm(side, uplo, trans, diag, m, n, alpha, A, B, C, layout="interleaved", ws=None,
+          stream=None, precision=None):
+    """Triangular product into C (written, not read, must not be B):
+    side "L": C = alpha op(tri(A)) B;  side "R": C = alpha B op(tri(A));
+    tri(A) = the uplo ("L"/"U") triangle of A, unit diagonal if diag == "U"."""
+    prec = precision_of(C.dtype, precision)
+    if A.dtype != C.dtype or B.dtype != C.dtype:
+        raise TypeError("A, B and C must share a dtype")
+    L = _abi.lib()
+    lda, psA, _ = geometry(A, layout)
+    ldb, psB, _ = geometry(B, layout)
+    ldc, psC, _ = geometry(C, layout)
+    args = ({"L": 0, "R": 1}[side], {"L": 0, "U": 1}[uplo], _abi.OP[trans],
+            {"N": 0, "U": 1}[diag], m, n)
+    need = L.qtrmm_workspace_bytes(*args, _abi.LAYOUT[layout], _abi.PRECISION[prec])
+    if ws is None:
+        ws = workspace(need, C.device)
+    wptr = ws.data_ptr() if ws is not None else None
+    wbytes = ws.numel() * ws.element_size() if ws is not None else 0
+    rc = L.qtrmm(*args, _abi.q4(alpha), A.data_ptr(), lda, psA, B.data_ptr(), ldb, psB,
+                 C.data_ptr(), ldc, psC, _abi.LAYOUT[layout], _abi.PRECISION[prec], wptr, wbytes,
+                 _stream_handle(stream))
+    _abi.check(rc, "qtrmm")
+    return C
+
+
 def qgemm_backward(X, W, dY, mb, k, n, dX=None, dW=None, accumulate=False,
                    layout="interleaved", ws=None, stream=None, precision=None):
     """dX = dY W^H and dW = X^H dY for Y = X W (either output may be None)."""

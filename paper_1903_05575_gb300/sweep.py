@@ -9,6 +9,8 @@ N x N products, Sec. 5), printing one JSON line per case:
          error, speedup over the FP64 rate at the same size.
   sliced: the digit-sliced FP64 path (FP64 data on the BF16 tensor cores),
          m = n = k in --sliced-sizes, the --ops pairs, both layouts.
+  trmm:  qtrmm (left, lower, op N) at --trmm sizes on every precision, with
+         its time relative to the GEMM of the same size.
 
 Timing: CUDA events on the launching stream around `reps` calls after
 warm-up; inputs of every case are larger than L2 except the smallest FP64
@@ -114,6 +116,47 @@ def split_case(n, kind, fp64_tflops, reps):
             "tolerance": 2e-6, "speedup_vs_fp64": tf / fp64_tflops}
 
 
+def trmm_case(n, precision, reps):
+    """qtrmm side L, lower, op N, m = n: effective TFLOP/s on the triangular
+    product's own work (16 n^3: half the GEMM's), its time relative to the
+    GEMM of the same size and precision, sampled error against the oracle's
+    triangular product."""
+    import torch
+
+    import qsynth
+    from . import ops
+    dev = torch.device("cuda", torch.cuda.current_device())
+    dt = torch.float32 if precision == "split_bf16" else torch.float64
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(5 * n)
+    A = torch.randn((n, n, 4), dtype=dt, device=dev, generator=gen)
+    B = torch.randn((n, n, 4), dtype=dt, device=dev, generator=gen)
+    C = torch.empty((n, n, 4), dtype=dt, device=dev)
+    al = qsynth.unit_quaternion(n + 5)
+    p = None if precision == "split_bf16" else precision
+    tr = _timed(lambda: ops.qtrmm("L", "L", "N", "N", n, n, al, A, B, C, precision=p), reps)
+    gm = _timed(lambda: ops.qgemm("N", "N", n, n, n, al, A, B, (0, 0, 0, 0), C, precision=p),
+                reps)
+    ops.qtrmm("L", "L", "N", "N", n, n, al, A, B, C, precision=p)
+    torch.cuda.synchronize()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    from oracle import oracle as orc
+    g = np.random.default_rng(4)
+    rows, cols = g.integers(0, n, 128), g.integers(0, n, 128)
+    Ah = A.double().cpu().numpy().copy()
+    idx = np.arange(n)
+    Ah[idx[:, None] > idx[None, :]] = 0.0  # stored (column, row): keep row >= column
+    ref = orc.qgemm_entries("N", "N", n, n, n, al, Ah, B.double().cpu().numpy(), np.zeros(4),
+                            np.zeros_like(Ah), rows, cols)
+    got = qsynth.components(C.double().cpu().numpy(), n, "interleaved")[rows, cols]
+    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    return {"path": "trmm_" + precision, "n": n, "side": "L", "uplo": "L", "op": "N",
+            "ms": tr, "gemm_ms": gm, "trmm_over_gemm_time": tr / gm,
+            "tflops_trmm_work": 16.0 * n ** 3 / (tr * 1e-3) / 1e12, "rel_err_sampled": err}
+
+
 def complex_comparison(n, reps, qgemm_ms=None):
     """The paper's experiment (Sec. 5, Fig. 4) on this GPU: the same product
     through cuBLAS ZGEMM on the 2n x 2n complex representation (Eq. qmat_complex,
@@ -159,6 +202,7 @@ def main():
     ap.add_argument("--layouts", default="interleaved,planes")
     ap.add_argument("--split-sizes", default="2048,8192")
     ap.add_argument("--sliced-sizes", default="")
+    ap.add_argument("--trmm", default="", help="sizes for the triangular product")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--compare", default="", help="sizes for the cuBLAS ZGEMM/DGEMM comparison")
     a = ap.parse_args()
@@ -186,6 +230,9 @@ def main():
         base = fp64_rate.get(n, peak)
         for kind in ("normal", "scaled"):
             print(json.dumps(split_case(n, kind, base, max(a.reps, 3))), flush=True)
+    for n in [int(x) for x in a.trmm.split(",") if x]:
+        for prec in ("fp64", "fp64_sliced", "split_bf16"):
+            print(json.dumps(trmm_case(n, prec, 2 if prec == "fp64" else 5)), flush=True)
     for n in [int(x) for x in a.compare.split(",") if x]:
         print(json.dumps(complex_comparison(n, a.reps)), flush=True)
 
