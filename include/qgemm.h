@@ -51,7 +51,8 @@
  *                          columns span many binades along k lose digits of
  *                          their small entries).  A row or column holding Inf
  *                          or NaN gives NaN in the matching row or column of
- *                          the product.  Needs a workspace.
+ *                          the product.  Needs a workspace; k <= 2^21
+ *                          (QGEMM_ERR_UNSUPPORTED above).
  *
  * Memory and streams: every matrix pointer is a DEVICE pointer owned by the
  * caller; alpha and beta are HOST arrays of 4 doubles, read during the call

@@ -67,6 +67,10 @@ def _bind(path):
                                  dp, dp, i64, i64, dp, i64, i64, dp, i64, i64, ctypes.c_int,
                                  ctypes.c_int]
     lib.oracle_qtrmm.restype = ctypes.c_int
+    lib.oracle_qgemm_mixed.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       i64, i64, i64, dp, dp, i64, i64, dp, i64, i64, dp, dp,
+                                       i64, i64, ctypes.c_int, ctypes.c_int]
+    lib.oracle_qgemm_mixed.restype = ctypes.c_int
     lib.oracle_max_threads.argtypes = []
     lib.oracle_max_threads.restype = ctypes.c_int
     return lib
@@ -193,4 +197,41 @@ def qtrmm(side, uplo, trans, diag, m, n, alpha, A, B, C, layout="interleaved", n
                           ldb, psB, _dptr(C), ldc, psC, LAYOUTS[layout], int(nthreads))
     if rc != 0:
         raise ValueError("oracle_qtrmm returned %d" % rc)
+    return C
+
+
+TYPES = {"H": 0, "C": 1, "R": 2}
+WIDTH = {"H": 4, "C": 2, "R": 1}
+
+
+def typed_geometry(X, layout, typ):
+    """(ld, plane_stride) of a typed operand: interleaved (cols, ld, width)
+    (a real operand may also be (cols, ld)); planes (width, cols, ld)."""
+    w = WIDTH[typ]
+    if layout == "interleaved":
+        if typ == "R" and X.ndim == 2:
+            return X.shape[1], 0
+        assert X.ndim == 3 and X.shape[2] == w
+        return X.shape[1], 0
+    assert X.ndim == 3 and X.shape[0] == w
+    return X.shape[2], X.shape[1] * X.shape[2]
+
+
+def qgemm_mixed(typeA, typeB, opA, opB, m, n, k, alpha, A, B, beta, C, layout="interleaved",
+                nthreads=0, lib=None):
+    """C <- alpha op(A) op(B) + beta C with A, B quaternion ("H"), complex ("C")
+    or real ("R"); C quaternion, in place."""
+    lib = lib or _load()
+    for X in (A, B, C):
+        _check(X)
+    lda, psA = typed_geometry(A, layout, typeA)
+    ldb, psB = typed_geometry(B, layout, typeB)
+    ldc, psC, _ = geometry(C, layout)
+    al = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64).reshape(4))
+    be = np.ascontiguousarray(np.asarray(beta, dtype=np.float64).reshape(4))
+    rc = lib.oracle_qgemm_mixed(TYPES[typeA], TYPES[typeB], OPS[opA], OPS[opB], m, n, k,
+                                _dptr(al), _dptr(A), lda, psA, _dptr(B), ldb, psB, _dptr(be),
+                                _dptr(C), ldc, psC, LAYOUTS[layout], int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_qgemm_mixed returned %d" % rc)
     return C

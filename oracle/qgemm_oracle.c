@@ -378,6 +378,72 @@ int oracle_qtrmm(int side, int uplo, int trans, int diag, int64_t m, int64_t n,
     return 0;
 }
 
+/*
+ * Mixed-type GEMM (the quaternion-complex and quaternion-real arithmetic the
+ * paper's library provides next to HGEMM, Sec. 5):
+ *   C <- alpha op(A) op(B) + beta C,   C quaternion,
+ * with A and B each quaternion (type 0), complex (type 1: z = z^0 e0 + z^1 e1,
+ * the complex subalgebra of H, Sec. 2.1) or real (type 2: x e0).  The
+ * plain definition: every operand entry is the quaternion it is (missing
+ * components zero) and the product is the quaternion GEMM above.
+ * Storage: interleaved, 4 / 2 / 1 reals per element (component s of (r, c)
+ * at w*(r + c*ld) + s, w the width); split planes, 4 / 2 / 1 planes at the
+ * plane stride.
+ */
+static void load_typed(const double *X, int64_t ld, int64_t ps, int layout, int type,
+                       int64_t r, int64_t c, double q[4])
+{
+    const int w = type == 0 ? 4 : (type == 1 ? 2 : 1);
+    q[0] = q[1] = q[2] = q[3] = 0.0;
+    for (int s = 0; s < w; ++s)
+        q[s] = layout == ORACLE_INTERLEAVED ? X[w * (r + c * ld) + s] : X[s * ps + r + c * ld];
+}
+
+static void load_op_typed(const double *X, int64_t ld, int64_t ps, int layout, int type, int op,
+                          int64_t r, int64_t c, double q[4])
+{
+    if (op == ORACLE_OP_T || op == ORACLE_OP_H)
+        load_typed(X, ld, ps, layout, type, c, r, q);
+    else
+        load_typed(X, ld, ps, layout, type, r, c, q);
+    if (op == ORACLE_OP_C || op == ORACLE_OP_H) conjugate(q);
+}
+
+int oracle_qgemm_mixed(int typeA, int typeB, int opA, int opB, int64_t m, int64_t n, int64_t k,
+                       const double alpha[4], const double *A, int64_t lda, int64_t psA,
+                       const double *B, int64_t ldb, int64_t psB, const double beta[4],
+                       double *C, int64_t ldc, int64_t psC, int layout, int nthreads)
+{
+    if (m < 0 || n < 0 || k < 0) return -1;
+    if (typeA < 0 || typeA > 2 || typeB < 0 || typeB > 2) return -1;
+    if (opA < 0 || opA > 3 || opB < 0 || opB > 3) return -1;
+    if (layout != ORACLE_INTERLEAVED && layout != ORACLE_SPLIT_PLANES) return -1;
+    const int read_c = !is_zero(beta);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t j = 0; j < n; ++j) {
+        for (int64_t i = 0; i < m; ++i) {
+            double P[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int64_t kap = 0; kap < k; ++kap) {
+                double a[4], b[4], ab[4];
+                load_op_typed(A, lda, psA, layout, typeA, opA, i, kap, a);
+                load_op_typed(B, ldb, psB, layout, typeB, opB, kap, j, b);
+                oracle_hamilton(a, b, ab);
+                P[0] += ab[0]; P[1] += ab[1]; P[2] += ab[2]; P[3] += ab[3];
+            }
+            double cin[4], out[4];
+            if (read_c) load_stored(C, ldc, psC, layout, i, j, cin);
+            finish(alpha, P, beta, read_c ? cin : NULL, out);
+            store_stored(C, ldc, psC, layout, i, j, out);
+        }
+    }
+    return 0;
+}
+
 /* Number of OpenMP threads the oracle would use by default. */
 int oracle_max_threads(void)
 {

@@ -73,6 +73,9 @@ constexpr uint32_t kTmemCols = 512;                  // 6 regions x 64 used
 constexpr size_t kSmem = 1024 + SST * kStageBytes + 256;
 constexpr int kGroupM = 8;
 constexpr int kNonFinite = -0x40000000;              // exponent slot of a non-finite row
+// Largest quaternion k: the slicing grid (k/8 blocks <= 65535) and the 64-bit
+// level sums (2^46 per 256-k chunk) both stay in range.
+constexpr int64_t kMaxSlicedK = int64_t(1) << 21;
 
 struct SlicedParams {
   int64_t m, n;
@@ -1041,6 +1044,7 @@ int sliced_workspace_bytes(const GemmDesc &d, size_t *bytes) {
 }
 
 int launch_sliced_gemm(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_t stream) {
+  if (d.k > kMaxSlicedK) return QGEMM_ERR_UNSUPPORTED;
   const SlicedPlan pl = plan_for(d);
   if (ws == nullptr || ws_bytes < pl.total) return QGEMM_ERR_WORKSPACE;
   unsigned char *w = static_cast<unsigned char *>(ws);
@@ -1189,6 +1193,8 @@ int prepare_sliced_grouped(const std::vector<GemmDesc> &in, int layout, unsigned
                            size_t ws_bytes, cudaStream_t s, qgemm_grouped_plan *plan) {
   const GroupedLayout L = grouped_layout(in);
   if (ws_bytes < L.total) return -6;
+  for (const GemmDesc &d : in)
+    if (d.k > kMaxSlicedK) return QGEMM_ERR_UNSUPPORTED;
   if (L.tiles > 0x7fffffff || L.mtiles > 0x7fffffff || L.stiles > 0x7fffffff)
     return QGEMM_ERR_UNSUPPORTED;
   int rc = set_gemm_smem<true>();

@@ -101,3 +101,40 @@ def grouped_problems(count, seed, lo=8, hi=256, ops=("N", "H")):
 def stored_shape(op, rows, cols):
     """(stored rows, stored cols) of X such that op(X) is rows x cols."""
     return (cols, rows) if op in ("T", "H") else (rows, cols)
+
+
+WIDTH = {"H": 4, "C": 2, "R": 1}
+
+
+def typed(rows, cols, seed, typ, layout="interleaved", ld=None, kind="normal", pad=np.nan,
+          dtype=np.float64):
+    """A quaternion ("H"), complex ("C") or real ("R") matrix with iid N(0,1)
+    (kind "normal") or small-integer (kind "int", |x| <= 8) components:
+    interleaved (cols, ld, width), planes (width, cols, ld)."""
+    w = WIDTH[typ]
+    g = rng(seed)
+    if kind == "int":
+        v = g.integers(-8, 9, size=(rows, cols, w)).astype(np.float64)
+    else:
+        v = g.standard_normal((rows, cols, w))
+    ld = rows if ld is None else ld
+    ld = max(ld, 1)
+    if layout == "interleaved":
+        out = np.full((cols, ld, w), pad, dtype=dtype)
+        out[:, :rows, :] = np.transpose(v, (1, 0, 2))
+    else:
+        out = np.full((w, cols, ld), pad, dtype=dtype)
+        out[:, :, :rows] = np.transpose(v, (2, 1, 0))
+    return out
+
+
+def typed_components(X, rows, typ, layout):
+    """Typed storage -> (rows, cols, 4) quaternion components (missing ones 0)."""
+    w = WIDTH[typ]
+    if layout == "interleaved":
+        v = np.transpose(X[:, :rows, :], (1, 0, 2))
+    else:
+        v = np.transpose(X[:, :, :rows], (2, 1, 0))
+    out = np.zeros(v.shape[:2] + (4,))
+    out[..., :w] = v
+    return out

@@ -356,10 +356,75 @@ def pin_trmm_transpose_duality(lib):
     return np.array_equal(qsynth.components(got, m, "interleaved"), want)
 
 
+def _mixed_case(typeA, typeB, opA, opB, m, n, k, layout, seed, alpha, beta, lib):
+    ra, ca = qsynth.stored_shape(opA, m, k)
+    rb, cb = qsynth.stored_shape(opB, k, n)
+    A = qsynth.typed(ra, ca, seed, typeA, layout, ld=ra + 1, kind="int")
+    B = qsynth.typed(rb, cb, seed + 1, typeB, layout, ld=rb + 2, kind="int")
+    C = qsynth.small_int(m, n, seed + 2, layout, ld=m + 1)
+    got = C.copy()
+    orc.qgemm_mixed(typeA, typeB, opA, opB, m, n, k, alpha, A, B, beta, got, layout=layout,
+                    lib=lib)
+    Ao = qref.apply_op(qsynth.typed_components(A, ra, typeA, layout), opA)
+    Bo = qref.apply_op(qsynth.typed_components(B, rb, typeB, layout), opB)
+    return Ao, Bo, qsynth.components(C, m, layout), qsynth.components(got, m, layout)
+
+
+def pin_mixed_cayley_dickson(lib):
+    """Mixed-type products (quaternion-complex and quaternion-real, Sec. 5)
+    through a route that never forms a Hamilton product: with
+    q = z1 + z2 e2 (z1 = q^0 + q^1 e1, z2 = q^2 + q^3 e1) and w complex,
+    q w = z1 w + z2 conj(w) e2 and w q = w z1 + w z2 e2 (numpy complex
+    matmuls); a real factor scales every component.  Exact on small integers,
+    alpha = 1, beta = 0, every op, both layouts."""
+    one, zero = np.array([1.0, 0, 0, 0]), np.zeros(4)
+    m, n, k = 3, 4, 5
+
+    def cd(Q):
+        return Q[..., 0] + 1j * Q[..., 1], Q[..., 2] + 1j * Q[..., 3]
+
+    for layout in qsynth.LAYOUTS:
+        for opA in "NTCH":
+            for opB in "NTCH":
+                for tA, tB in (("H", "C"), ("C", "H"), ("C", "C"), ("H", "R"), ("R", "H"),
+                               ("R", "C")):
+                    Ao, Bo, _, G = _mixed_case(tA, tB, opA, opB, m, n, k, layout, 97, one, zero,
+                                               lib)
+                    z1, z2 = cd(Ao)
+                    w1, w2 = cd(Bo)
+                    want = np.zeros((m, n, 4))
+                    if tB != "H":          # right factor complex (or real): q w
+                        p1, p2 = z1 @ w1, z2 @ np.conj(w1)
+                    else:                  # left factor complex (or real): w q
+                        p1, p2 = z1 @ w1, z1 @ w2
+                    want[..., 0], want[..., 1] = p1.real, p1.imag
+                    want[..., 2], want[..., 3] = p2.real, p2.imag
+                    if not np.array_equal(G, want):
+                        return False
+    return True
+
+
+def pin_mixed_scalars(lib):
+    """alpha, beta on the left of a mixed product: equal to the complex
+    2x2 representation of alpha (op(A) op(B)) + beta C, exactly."""
+    alpha, beta = np.array([1.0, -2.0, 1.0, 3.0]), np.array([2.0, 0.0, -1.0, 1.0])
+    for tA, tB in (("H", "C"), ("R", "H")):
+        Ao, Bo, Cc, G = _mixed_case(tA, tB, "H", "N", 4, 3, 5, "planes", 98, alpha, beta, lib)
+        m, n = 4, 3
+        P = qref.to_complex(Ao) @ qref.to_complex(Bo)
+        want = qref.from_complex(np.kron(qref.scalar_complex(alpha), np.eye(m)) @ P
+                                 + np.kron(qref.scalar_complex(beta), np.eye(m))
+                                 @ qref.to_complex(Cc), m, n)
+        if not np.array_equal(G, want):
+            return False
+    return True
+
+
 PINS = [pin_basis_table, pin_worked_products, pin_norm_multiplicative, pin_complex_subalgebra,
         pin_scalar_complex_rep, pin_gemm_vs_complex, pin_conj_transpose_identity,
         pin_associative, pin_scalar_side, pin_blas_conventions, pin_entries_match_full,
-        pin_herk_vs_complex, pin_trmm_vs_complex, pin_trmm_transpose_duality]
+        pin_herk_vs_complex, pin_trmm_vs_complex, pin_trmm_transpose_duality,
+        pin_mixed_cayley_dickson, pin_mixed_scalars]
 
 
 def failing_pins(lib, pins=PINS):
@@ -424,6 +489,12 @@ MUTATIONS = {
                                    "        load_stored(A, lda, psA, layout, c, r, q);"),
     "trmm_right_side_order": ("                    load_stored(B, ldb, psB, layout, i, kap, a);\n                    load_op_tri(A, lda, psA, layout, uplo, diag, trans, kap, j, b);",
                               "                    load_stored(B, ldb, psB, layout, i, kap, b);\n                    load_op_tri(A, lda, psA, layout, uplo, diag, trans, kap, j, a);"),
+    "mixed_complex_width": ("const int w = type == 0 ? 4 : (type == 1 ? 2 : 1);",
+                            "const int w = type == 0 ? 4 : (type == 1 ? 1 : 1);"),
+    "mixed_no_conjugate": ("        load_typed(X, ld, ps, layout, type, r, c, q);\n    if (op == ORACLE_OP_C || op == ORACLE_OP_H) conjugate(q);",
+                           "        load_typed(X, ld, ps, layout, type, r, c, q);\n    if (op == ORACLE_OP_C) conjugate(q);"),
+    "mixed_planes_interleaved": ("X[w * (r + c * ld) + s] : X[s * ps + r + c * ld]",
+                                 "X[4 * (r + c * ld) + s] : X[s * ps + r + c * ld]"),
     "plane_stride_wrong": ("q[0] = e[0]; q[1] = e[ps]; q[2] = e[2 * ps]; q[3] = e[3 * ps];",
                            "q[0] = e[0]; q[1] = e[ps]; q[2] = e[3 * ps]; q[3] = e[2 * ps];"),
 }
