@@ -103,6 +103,10 @@ extern "C" {
 #define QGEMM_NON_UNIT 0
 #define QGEMM_UNIT 1
 
+#define QGEMM_TYPE_QUATERNION 0
+#define QGEMM_TYPE_COMPLEX 1
+#define QGEMM_TYPE_REAL 2
+
 #define QGEMM_FP64 0
 #define QGEMM_FP32_SPLIT_BF16 1
 #define QGEMM_FP64_SLICED_BF16 2
@@ -318,6 +322,34 @@ int qtrmm(int side, int uplo, int transA, int diag, int64_t m, int64_t n,
 /* Workspace qtrmm() needs (0 for invalid arguments or an empty C). */
 size_t qtrmm_workspace_bytes(int side, int uplo, int transA, int diag, int64_t m, int64_t n,
                              int layout, int precision);
+
+/*
+ * qgemm_mixed: mixed-type product (the quaternion-complex and
+ * quaternion-real arithmetic of the paper's library, Sec. 5):
+ *     C <- alpha op(A) op(B) + beta C,   C quaternion,
+ * with A and B each QGEMM_TYPE_QUATERNION, QGEMM_TYPE_COMPLEX (z = z^0 e0 +
+ * z^1 e1, the complex numbers inside H) or QGEMM_TYPE_REAL (x e0).  A complex
+ * element stores 2 reals, a real one 1: interleaved [z^0, z^1] (component s
+ * of (r, c) at w*(r + c*ld) + s, w = 2 or 1), split planes 2 or 1 planes at
+ * the plane stride.  op conjugates as in H (conj(z) = z^0 - z^1 e1).
+ * Arguments: 1 typeA, 2 typeB, then the arguments of qgemm() as 3..23
+ * (opA = 3 ... stream = 23) for the -i return.  On the tensor-core
+ * precisions a complex (real) factor halves (quarters) the MMAs of the
+ * quaternion product; the FP64 path runs the quaternion product on a
+ * quaternion copy of the narrow operands.  Workspace from
+ * qgemm_mixed_workspace_bytes() (also for QGEMM_FP64 with a narrow operand).
+ */
+int qgemm_mixed(int typeA, int typeB, int opA, int opB, int64_t m, int64_t n, int64_t k,
+                const double alpha[4],
+                const void *A, int64_t lda, int64_t psA,
+                const void *B, int64_t ldb, int64_t psB,
+                const double beta[4],
+                void *C, int64_t ldc, int64_t psC,
+                int layout, int precision,
+                void *workspace, size_t workspace_bytes, void *stream);
+
+size_t qgemm_mixed_workspace_bytes(int typeA, int typeB, int opA, int opB, int64_t m,
+                                   int64_t n, int64_t k, int layout, int precision);
 
 /*
  * qgemm_backward: gradients of a quaternion linear map Y = X W, with

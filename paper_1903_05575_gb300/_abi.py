@@ -64,6 +64,9 @@ SIGNATURES = {
     "qtrmm": (i32, [i32, i32, i32, i32, i64, i64, dp, vp, i64, i64, vp, i64, i64, vp, i64, i64,
                     i32, i32, vp, sz, vp]),
     "qtrmm_workspace_bytes": (sz, [i32, i32, i32, i32, i64, i64, i32, i32]),
+    "qgemm_mixed": (i32, [i32, i32, i32, i32, i64, i64, i64, dp, vp, i64, i64, vp, i64, i64, dp,
+                          vp, i64, i64, i32, i32, vp, sz, vp]),
+    "qgemm_mixed_workspace_bytes": (sz, [i32, i32, i32, i32, i64, i64, i64, i32, i32]),
     "qgemm_backward": (i32, [i64, i64, i64, vp, i64, i64, vp, i64, i64, vp, i64, i64,
                              vp, i64, i64, vp, i64, i64, i32, i32, i32, vp, sz, vp]),
     "qgemm_backward_workspace_bytes": (sz, [i64, i64, i64, i32, i32]),

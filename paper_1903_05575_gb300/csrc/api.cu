@@ -73,6 +73,8 @@ int validate_gemm(int opA, int opB, int64_t m, int64_t n, int64_t k, const doubl
   d->beta_zero = is_zero4(beta);
   d->tri = 0;
   d->krange = 0;
+  d->kwidth = 4;
+  d->swap = 0;
   return 0;
 }
 

@@ -98,6 +98,7 @@ struct MaxArgs {
   int64_t srows, scols;  // stored extent
   int layout;
   int by_col;            // 0: maxima per stored row, 1: per stored column
+  int width;             // components stored per element (4, 2 or 1)
   unsigned long long *out;
 };
 
@@ -114,6 +115,9 @@ struct SliceArgs {
   int layout;
   int row_contig;        // stored row index == op row
   uint32_t negmask;      // bit j: negate component j (conjugation)
+  int width;             // components stored per element (4, 2 or 1; the rest are 0)
+  int kw;                // components per kappa in the output (4; 2 or 1 for a
+                         // complex or real left operand)
 };
 
 // One problem of a grouped batch (device descriptor in the workspace).
@@ -681,9 +685,8 @@ __device__ __forceinline__ void max_tile(const MaxArgs &a, int64_t rt, int64_t c
     const int64_t c = c0 + ty + 8 * s;
     unsigned long long mx = 0;
     if (r < a.srows && c < a.scols) {
-#pragma unroll
-      for (int comp = 0; comp < 4; ++comp) {
-        const double x = a.layout == QGEMM_INTERLEAVED ? a.X[4 * (r + c * a.ld) + comp]
+      for (int comp = 0; comp < a.width; ++comp) {
+        const double x = a.layout == QGEMM_INTERLEAVED ? a.X[a.width * (r + c * a.ld) + comp]
                                                        : a.X[r + c * a.ld + comp * a.ps];
         const unsigned long long b =
             static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7fffffffffffffffull;
@@ -785,6 +788,16 @@ __device__ __forceinline__ void digits6(long long X, int (&d)[NSL]) {
 //   A: A'_t[r][4 kappa + j] = d_t(a^j)
 //   B: B'_t[4 r + c][4 kappa + j] = sign(j, j^c) d_t(b^(j^c))
 // Columns kappa >= kq up to kp/4 are zeros (K padding).
+// The first kw of four BF16 values at dst (aligned to kw values).
+__device__ __forceinline__ void store_kw(__nv_bfloat16 *dst, const __nv_bfloat16 (&w)[4], int kw) {
+  if (kw == 4)
+    *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(w);
+  else if (kw == 2)
+    *reinterpret_cast<uint32_t *>(dst) = *reinterpret_cast<const uint32_t *>(w);
+  else
+    dst[0] = w[0];
+}
+
 struct SliceSmem {
   double4 tile[32][33];
   int shift[32];  // 47 - e of each row; kNonFinite for a row with Inf or NaN
@@ -815,13 +828,15 @@ __device__ __forceinline__ void slice_tile(const SliceArgs &p, int64_t rt, int64
     double4 v = make_double4(0.0, 0.0, 0.0, 0.0);
     if (r < p.rows && kq < p.kq) {
       const int64_t sr = p.row_contig ? r : kq, sc = p.row_contig ? kq : r;
+      double e4[4] = {0.0, 0.0, 0.0, 0.0};
       if (p.layout == QGEMM_INTERLEAVED) {
-        const double *e = p.X + 4 * (sr + sc * p.ld);
-        v = make_double4(e[0], e[1], e[2], e[3]);
+        const double *e = p.X + p.width * (sr + sc * p.ld);
+        for (int q = 0; q < p.width; ++q) e4[q] = e[q];
       } else {
         const double *e = p.X + sr + sc * p.ld;
-        v = make_double4(e[0], e[p.ps], e[2 * p.ps], e[3 * p.ps]);
+        for (int q = 0; q < p.width; ++q) e4[q] = e[q * p.ps];
       }
+      v = make_double4(e4[0], e4[1], e4[2], e4[3]);
       if (p.negmask & 2u) v.y = -v.y;
       if (p.negmask & 4u) v.z = -v.z;
       if (p.negmask & 8u) v.w = -v.w;
@@ -833,7 +848,7 @@ __device__ __forceinline__ void slice_tile(const SliceArgs &p, int64_t rt, int64
   for (int s = 0; s < 4; ++s) {
     const int kk = tx, rr = ty + 8 * s;
     const int64_t r = r0 + rr, kq = k0 + kk;
-    if (r >= p.rows || 4 * kq >= p.kp) continue;
+    if (r >= p.rows || p.kw * kq >= p.kp) continue;
     const double4 v = tile[kk][rr];
     const int sft = sm.shift[rr];
     const double comp[4] = {v.x, v.y, v.z, v.w};
@@ -844,11 +859,11 @@ __device__ __forceinline__ void slice_tile(const SliceArgs &p, int64_t rt, int64
     if (!IS_B) {
 #pragma unroll
       for (int t = 0; t < NSL; ++t) {
-        __nv_bfloat16 *dst = p.out + t * p.slice_stride + r * p.kp + 4 * kq;
+        __nv_bfloat16 *dst = p.out + t * p.slice_stride + r * p.kp + p.kw * kq;
         __align__(8) __nv_bfloat16 w[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) w[j] = __float2bfloat16_rn(static_cast<float>(d[j][t]));
-        *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(w);
+        store_kw(dst, w, p.kw);
       }
     } else {
 #pragma unroll
@@ -862,8 +877,8 @@ __device__ __forceinline__ void slice_tile(const SliceArgs &p, int64_t rt, int64
             const int x = basis_sign(j, q) < 0 ? -d[q][t] : d[q][t];
             w[j] = __float2bfloat16_rn(static_cast<float>(x));
           }
-          __nv_bfloat16 *dst = p.out + t * p.slice_stride + (4 * r + c) * p.kp + 4 * kq;
-          *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(w);
+          __nv_bfloat16 *dst = p.out + t * p.slice_stride + (4 * r + c) * p.kp + p.kw * kq;
+          store_kw(dst, w, p.kw);
         }
     }
   }
@@ -901,7 +916,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 SlicedPlan plan_for(const GemmDesc &d) {
   SlicedPlan s;
-  s.kp = ((4 * d.k + SBK - 1) / SBK) * SBK;
+  s.kp = ((d.kwidth * d.k + SBK - 1) / SBK) * SBK;
   s.a_off = 0;
   const size_t a_bytes = static_cast<size_t>(NSL) * d.m * s.kp * 2;
   s.b_off = align_up(a_bytes, 1024);
@@ -938,12 +953,13 @@ MaxArgs max_args(const MatView &v, bool by_col, int layout, unsigned long long *
   a.scols = v.cols;
   a.layout = layout;
   a.by_col = by_col ? 1 : 0;
+  a.width = v.width;
   a.out = out;
   return a;
 }
 
 SliceArgs slice_args(bool is_b, const MatView &v, int op, int64_t rows, int64_t kq, int64_t kp,
-                     int layout, __nv_bfloat16 *out, const unsigned long long *maxbits,
+                     int kw, int layout, __nv_bfloat16 *out, const unsigned long long *maxbits,
                      int *eout) {
   SliceArgs a;
   a.X = static_cast<const double *>(v.ptr);
@@ -959,6 +975,8 @@ SliceArgs slice_args(bool is_b, const MatView &v, int op, int64_t rows, int64_t 
   a.layout = layout;
   a.row_contig = is_b ? (op_trans(op) ? 1 : 0) : (op_trans(op) ? 0 : 1);
   a.negmask = op_conj(op) ? 0xEu : 0u;
+  a.width = v.width;
+  a.kw = kw;
   return a;
 }
 
@@ -976,7 +994,7 @@ int launch_max(const MaxArgs &a, cudaStream_t stream) {
 }
 
 int launch_slices(bool is_b, const SliceArgs &a, cudaStream_t stream) {
-  const int64_t gx = (a.rows + 31) / 32, gy = (a.kp / 4 + 31) / 32;
+  const int64_t gx = (a.rows + 31) / 32, gy = (a.kp / a.kw + 31) / 32;
   if (gx > 0x7fffffff || gy > 65535) return QGEMM_ERR_UNSUPPORTED;
   dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy));
   if (is_b)
@@ -1000,6 +1018,7 @@ SlicedParams params_for(const GemmDesc &d, int64_t kp, const int *ea, const int 
   g.alpha_real = (d.alpha[1] == 0.0 && d.alpha[2] == 0.0 && d.alpha[3] == 0.0) ? 1 : 0;
   g.beta_real = (d.beta[1] == 0.0 && d.beta[2] == 0.0 && d.beta[3] == 0.0) ? 1 : 0;
   g.krange = d.krange;
+  g.swap = d.swap;
   g.c_vec2 = (reinterpret_cast<uintptr_t>(d.C) % 16 == 0) ? 1 : 0;
   g.C = static_cast<double *>(d.C);
   g.ldc = d.ldc;
@@ -1061,10 +1080,12 @@ int launch_sliced_gemm(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_
   if (rc) return rc;
   rc = launch_max(max_args(d.B, max_by_col(true, d.opB), d.layout, maxb), stream);
   if (rc) return rc;
-  rc = launch_slices(false, slice_args(false, d.A, d.opA, d.m, d.k, pl.kp, d.layout, wa, maxa, ea),
+  rc = launch_slices(false, slice_args(false, d.A, d.opA, d.m, d.k, pl.kp, d.kwidth, d.layout, wa,
+                                      maxa, ea),
                      stream);
   if (rc) return rc;
-  rc = launch_slices(true, slice_args(true, d.B, d.opB, d.n, d.k, pl.kp, d.layout, wb, maxb, eb),
+  rc = launch_slices(true, slice_args(true, d.B, d.opB, d.n, d.k, pl.kp, d.kwidth, d.layout, wb,
+                                      maxb, eb),
                      stream);
   if (rc) return rc;
 
@@ -1222,8 +1243,8 @@ int prepare_sliced_grouped(const std::vector<GemmDesc> &in, int layout, unsigned
       const bool bca = max_by_col(false, d.opA), bcb = max_by_col(true, d.opB);
       q.ma = max_args(d.A, bca, layout, maxa);
       q.mb = max_args(d.B, bcb, layout, maxb);
-      q.sa = slice_args(false, d.A, d.opA, d.m, d.k, kp, layout, wa, maxa, ea);
-      q.sb = slice_args(true, d.B, d.opB, d.n, d.k, kp, layout, wb, maxb, eb);
+      q.sa = slice_args(false, d.A, d.opA, d.m, d.k, kp, 4, layout, wa, maxa, ea);
+      q.sb = slice_args(true, d.B, d.opB, d.n, d.k, kp, 4, layout, wb, maxb, eb);
       if (!encode_slices(&q.tmA, wa, kp, d.m, SBM) || !encode_slices(&q.tmB, wb, kp, 4 * d.n, SBN))
         return QGEMM_ERR_UNSUPPORTED;
       const MatView *v[2] = {&d.A, &d.B};

@@ -398,6 +398,8 @@ int prepare_split(const std::vector<GemmDesc> &ds_in, int layout, unsigned char 
         a.layout = layout;
         a.row_contig = is_b ? (op_trans(op) ? 1 : 0) : (op_trans(op) ? 0 : 1);
         a.negmask = op_conj(op) ? 0xEu : 0u;
+        a.width = 4;
+        a.kw = 4;
       };
       prep(q.pa, d.A, d.opA, false, d.m, wa);
       prep(q.pb, d.B, d.opB, true, d.n, wb);

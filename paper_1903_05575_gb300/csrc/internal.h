@@ -14,9 +14,10 @@ namespace qg {
 // cs = 1, rs = 4, ld = 4*ld_q.  Split planes: cs = plane stride, rs = 1.
 struct MatView {
   const void *ptr;
-  int64_t rows, cols;  // stored extent (quaternions)
-  int64_t ld;          // leading dimension (quaternions)
+  int64_t rows, cols;  // stored extent (elements)
+  int64_t ld;          // leading dimension (elements)
   int64_t ps;          // plane stride (reals, split layout only)
+  int width = 4;       // components stored per element: 4 quaternion, 2 complex, 1 real
 };
 
 // Description of one GEMM after validation.
@@ -29,11 +30,17 @@ struct GemmDesc {
   int64_t ldc, psc;
   int layout;
   bool beta_zero;
-  int tri;  // 0: full C; 1: lower triangle only; 2: upper (Hermitian rank-k update)
+  int tri = 0;  // 0: full C; 1: lower triangle only; 2: upper (Hermitian rank-k update)
   // k-range of an output tile when one operand is triangular (qtrmm): 0 all
   // of K; 1 kappa < tile row end; 2 kappa >= tile row start; 3 kappa >= tile
   // column start; 4 kappa < tile column end.
-  int krange;
+  int krange = 0;
+  // Mixed types (qgemm_mixed): components of op(A) per kappa in the real
+  // form (A.width: 4, or 2 / 1 for a complex / real left operand, so K' =
+  // kwidth * k), and swap = 1 when the product was turned around,
+  // D = op(B)^H op(A)^H, and C = conj(D)^T is stored.
+  int kwidth = 4;
+  int swap = 0;
 };
 
 inline bool op_trans(int op) { return op == QGEMM_OP_T || op == QGEMM_OP_H; }

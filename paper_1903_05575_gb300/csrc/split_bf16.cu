@@ -90,7 +90,7 @@ struct SplitPlan {
 
 SplitPlan plan_for(const GemmDesc &d) {
   SplitPlan s;
-  s.kp = ((4 * d.k + BK - 1) / BK) * BK;
+  s.kp = ((d.kwidth * d.k + BK - 1) / BK) * BK;
   s.a_bytes = static_cast<size_t>(TERMS) * d.m * s.kp * 2;
   s.b_bytes = static_cast<size_t>(TERMS) * 4 * d.n * s.kp * 2;
   s.b_offset = (s.a_bytes + 1023) & ~static_cast<size_t>(1023);
@@ -112,6 +112,7 @@ GemmParams gemm_params(const GemmDesc &d, int64_t kp) {
   g.beta_zero = d.beta_zero ? 1 : 0;
   g.tri = d.tri;
   g.krange = d.krange;
+  g.swap = d.swap;
   g.c_vec4 = (reinterpret_cast<uintptr_t>(d.C) % 16 == 0) ? 1 : 0;
   for (int s = 0; s < 4; ++s) {
     g.alpha[s] = static_cast<float>(d.alpha[s]);
@@ -167,7 +168,8 @@ int set_smem(K kern, size_t bytes) {
 }
 
 int launch_prepass(bool is_b, const MatView &v, int op, int64_t rows, int64_t kq, int64_t kp,
-                   int layout, __nv_bfloat16 *out, int64_t term_stride, cudaStream_t stream) {
+                   int kw, int layout, __nv_bfloat16 *out, int64_t term_stride,
+                   cudaStream_t stream) {
   PrepArgs a;
   a.X = static_cast<const float *>(v.ptr);
   a.ld = v.ld;
@@ -181,7 +183,9 @@ int launch_prepass(bool is_b, const MatView &v, int op, int64_t rows, int64_t kq
   // A: op row i is the stored row for N/C; B: op row n is the stored row for T/H
   a.row_contig = is_b ? (op_trans(op) ? 1 : 0) : (op_trans(op) ? 0 : 1);
   a.negmask = op_conj(op) ? 0xEu : 0u;
-  const int64_t gx = (rows + 31) / 32, gy = (kp / 4 + 31) / 32;
+  a.width = v.width;
+  a.kw = kw;
+  const int64_t gx = (rows + 31) / 32, gy = (kp / kw + 31) / 32;
   if (gx > 0x7fffffff || gy > 65535) return QGEMM_ERR_UNSUPPORTED;
   dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy));
   if (is_b)
@@ -200,6 +204,10 @@ namespace {
 
 // The fused single-problem path (no workspace) is taken when the caller asks
 // for it with QGEMM_SPLIT_FUSED=1 and every operand is TMA-addressable.
+bool plain_quaternion(const GemmDesc &d) {
+  return d.kwidth == 4 && d.A.width == 4 && d.B.width == 4 && !d.swap;
+}
+
 bool want_fused() {
   const char *e = std::getenv("QGEMM_SPLIT_FUSED");
   return e && e[0] == '1';
@@ -238,7 +246,7 @@ int launch_fused_single(const GemmDesc &d, const CUtensorMap &tmA, const CUtenso
 }  // namespace
 
 int split_workspace_bytes(const GemmDesc &d, size_t *bytes) {
-  if (want_fused() && d.k > 0 && d.m > 0 && d.n > 0) {
+  if (want_fused() && plain_quaternion(d) && d.k > 0 && d.m > 0 && d.n > 0) {
     CUtensorMap a, b;
     if (fused_maps(d, &a, &b)) {
       *bytes = 0;
@@ -254,7 +262,7 @@ int split_workspace_bytes(const GemmDesc &d, size_t *bytes) {
 }
 
 int launch_split_gemm(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_t stream) {
-  if (want_fused()) {
+  if (want_fused() && plain_quaternion(d)) {
     CUtensorMap fa, fb;
     std::memset(&fa, 0, sizeof(fa));
     std::memset(&fb, 0, sizeof(fb));
@@ -264,9 +272,11 @@ int launch_split_gemm(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_t
   if (ws_bytes < pl.total || ws == nullptr) return QGEMM_ERR_WORKSPACE;
   auto *wa = static_cast<__nv_bfloat16 *>(ws);
   auto *wb = reinterpret_cast<__nv_bfloat16 *>(static_cast<unsigned char *>(ws) + pl.b_offset);
-  int rc = launch_prepass(false, d.A, d.opA, d.m, d.k, pl.kp, d.layout, wa, d.m * pl.kp, stream);
+  int rc = launch_prepass(false, d.A, d.opA, d.m, d.k, pl.kp, d.kwidth, d.layout, wa,
+                          d.m * pl.kp, stream);
   if (rc) return rc;
-  rc = launch_prepass(true, d.B, d.opB, d.n, d.k, pl.kp, d.layout, wb, 4 * d.n * pl.kp, stream);
+  rc = launch_prepass(true, d.B, d.opB, d.n, d.k, pl.kp, d.kwidth, d.layout, wb, 4 * d.n * pl.kp,
+                      stream);
   if (rc) return rc;
 
   CUtensorMap tmA, tmB;

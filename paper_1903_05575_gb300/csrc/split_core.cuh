@@ -160,9 +160,13 @@ __device__ __forceinline__ Split3 split3(float x) {
 // ----------------------------------------------------------- pre-pass ---
 // One 32 x 32 tile of the op-matrix X (rows r = i for A or n for B; columns
 // kappa), read coalesced from the stored layout through shared memory, split,
-// and written K-major.  For A:  A'_t[r][4 kappa + j]  (row pitch kp).
-// For B:  B'_t[4 r + c][4 kappa + j] = sign(j, j^c) * t(b^(j^c))  (row pitch kp).
-// Columns kappa >= kq up to kp/4 are written as zeros (K padding).
+// and written K-major with kw components per kappa (4; 2 or 1 when the left
+// operand is complex or real, whose missing components are zero):
+//   A:  A'_t[r][kw kappa + j]                            j < kw
+//   B:  B'_t[4 r + c][kw kappa + j] = sign(j, j^c) * t(b^(j^c))
+// (row pitch kp).  Columns kappa >= kq up to kp/kw are zeros (K padding).
+// An operand stores `width` components per element (4, 2 or 1); the rest
+// read as zero.
 struct PrepArgs {
   const float *X;
   int64_t ld, ps;       // stored leading dimension, plane stride
@@ -174,12 +178,40 @@ struct PrepArgs {
   int layout;
   int row_contig;       // stored row index == op row (contiguous along r)
   uint32_t negmask;     // bit j: negate component j of the input (conjugation)
-  int pad;
+  int width;            // components stored per element
+  int kw;               // components per kappa in the output
 };
 
-template <bool IS_B>
-__device__ __forceinline__ void prep_tile(const PrepArgs &p, int64_t rt, int64_t kt,
-                                          float4 (*tile)[33]) {
+__device__ __forceinline__ float4 load_elem(const PrepArgs &p, int64_t sr, int64_t sc) {
+  float v[4] = {0.f, 0.f, 0.f, 0.f};
+  if (p.layout == QGEMM_INTERLEAVED) {
+    const float *e = p.X + p.width * (sr + sc * p.ld);
+    if (p.width == 4) {
+      v[0] = e[0]; v[1] = e[1]; v[2] = e[2]; v[3] = e[3];
+    } else {
+      for (int s = 0; s < p.width; ++s) v[s] = e[s];
+    }
+  } else {
+    const float *e = p.X + sr + sc * p.ld;
+    for (int s = 0; s < p.width; ++s) v[s] = e[s * p.ps];
+  }
+  return make_float4(v[0], v[1], v[2], v[3]);
+}
+
+template <int KW>
+__device__ __forceinline__ void store_terms(__nv_bfloat16 *dst, const __nv_bfloat16 (&w)[4]) {
+  if (KW == 4) {
+    *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(w);
+  } else if (KW == 2) {
+    *reinterpret_cast<uint32_t *>(dst) = *reinterpret_cast<const uint32_t *>(w);
+  } else {
+    dst[0] = w[0];
+  }
+}
+
+template <bool IS_B, int KW>
+__device__ __forceinline__ void prep_tile_kw(const PrepArgs &p, int64_t rt, int64_t kt,
+                                             float4 (*tile)[33]) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   const int64_t r0 = rt * 32, k0 = kt * 32;
 #pragma unroll
@@ -190,14 +222,7 @@ __device__ __forceinline__ void prep_tile(const PrepArgs &p, int64_t rt, int64_t
     const int64_t r = r0 + rr, kq = k0 + kk;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (r < p.rows && kq < p.kq) {
-      const int64_t sr = p.row_contig ? r : kq, sc = p.row_contig ? kq : r;
-      if (p.layout == QGEMM_INTERLEAVED) {
-        const float *e = p.X + 4 * (sr + sc * p.ld);
-        v = make_float4(e[0], e[1], e[2], e[3]);
-      } else {
-        const float *e = p.X + sr + sc * p.ld;
-        v = make_float4(e[0], e[p.ps], e[2 * p.ps], e[3 * p.ps]);
-      }
+      v = load_elem(p, p.row_contig ? r : kq, p.row_contig ? kq : r);
       if (p.negmask & 2u) v.y = -v.y;
       if (p.negmask & 4u) v.z = -v.z;
       if (p.negmask & 8u) v.w = -v.w;
@@ -209,7 +234,7 @@ __device__ __forceinline__ void prep_tile(const PrepArgs &p, int64_t rt, int64_t
   for (int s = 0; s < 4; ++s) {
     const int kk = tx, rr = ty + 8 * s;
     const int64_t r = r0 + rr, kq = k0 + kk;
-    if (r >= p.rows || 4 * kq >= p.kp) continue;
+    if (r >= p.rows || KW * kq >= p.kp) continue;
     const float4 v = tile[kk][rr];
     const float comp[4] = {v.x, v.y, v.z, v.w};
     Split3 sp[4];
@@ -218,9 +243,8 @@ __device__ __forceinline__ void prep_tile(const PrepArgs &p, int64_t rt, int64_t
     if (!IS_B) {
 #pragma unroll
       for (int t = 0; t < TERMS; ++t) {
-        __nv_bfloat16 *dst = p.out + t * p.term_stride + r * p.kp + 4 * kq;
         __align__(8) __nv_bfloat16 w[4] = {sp[0].t[t], sp[1].t[t], sp[2].t[t], sp[3].t[t]};
-        *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(w);
+        store_terms<KW>(p.out + t * p.term_stride + r * p.kp + KW * kq, w);
       }
     } else {
 #pragma unroll
@@ -234,11 +258,21 @@ __device__ __forceinline__ void prep_tile(const PrepArgs &p, int64_t rt, int64_t
             const __nv_bfloat16 x = sp[q].t[t];
             w[j] = basis_sign(j, q) < 0 ? __hneg(x) : x;
           }
-          __nv_bfloat16 *dst = p.out + t * p.term_stride + (4 * r + c) * p.kp + 4 * kq;
-          *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(w);
+          store_terms<KW>(p.out + t * p.term_stride + (4 * r + c) * p.kp + KW * kq, w);
         }
     }
   }
+}
+
+template <bool IS_B>
+__device__ __forceinline__ void prep_tile(const PrepArgs &p, int64_t rt, int64_t kt,
+                                          float4 (*tile)[33]) {
+  if (p.kw == 4)
+    prep_tile_kw<IS_B, 4>(p, rt, kt, tile);
+  else if (p.kw == 2)
+    prep_tile_kw<IS_B, 2>(p, rt, kt, tile);
+  else
+    prep_tile_kw<IS_B, 1>(p, rt, kt, tile);
 }
 
 // --------------------------------------------------------- GEMM params ---

@@ -106,6 +106,52 @@ def qherk(uplo, trans, n, k, alpha, A, beta, C, layout="interleaved", ws=None, s
     return C
 
 
+_WIDTH = {"H": 4, "C": 2, "R": 1}
+_TYPE = {"H": 0, "C": 1, "R": 2}
+
+
+def typed_geometry(X, layout, typ):
+    """(ld, plane_stride) of a quaternion ("H"), complex ("C") or real ("R")
+    tensor: interleaved (cols, ld, width) (a real one may be (cols, ld));
+    planes (width, cols, ld)."""
+    if not X.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    w = _WIDTH[typ]
+    if layout == "interleaved":
+        if typ == "R" and X.dim() == 2:
+            return X.shape[1], 0
+        if X.dim() != 3 or X.shape[2] != w:
+            raise ValueError("interleaved %s tensors have shape (cols, ld, %d)" % (typ, w))
+        return X.shape[1], 0
+    if X.dim() != 3 or X.shape[0] != w:
+        raise ValueError("split-plane %s tensors have shape (%d, cols, ld)" % (typ, w))
+    return X.shape[2], X.shape[1] * X.shape[2]
+
+
+def qgemm_mixed(typeA, typeB, opA, opB, m, n, k, alpha, A, B, beta, C, layout="interleaved",
+                ws=None, stream=None, precision=None):
+    """C <- alpha op(A) op(B) + beta C with A, B quaternion ("H"), complex ("C")
+    or real ("R") and C quaternion (in place)."""
+    prec = precision_of(C.dtype, precision)
+    if A.dtype != C.dtype or B.dtype != C.dtype:
+        raise TypeError("A, B and C must share a dtype")
+    L = _abi.lib()
+    lda, psA = typed_geometry(A, layout, typeA)
+    ldb, psB = typed_geometry(B, layout, typeB)
+    ldc, psC, _ = geometry(C, layout)
+    head = (_TYPE[typeA], _TYPE[typeB], _abi.OP[opA], _abi.OP[opB], m, n, k)
+    need = L.qgemm_mixed_workspace_bytes(*head, _abi.LAYOUT[layout], _abi.PRECISION[prec])
+    if ws is None:
+        ws = workspace(need, C.device)
+    wptr = ws.data_ptr() if ws is not None else None
+    wbytes = ws.numel() * ws.element_size() if ws is not None else 0
+    rc = L.qgemm_mixed(*head, _abi.q4(alpha), A.data_ptr(), lda, psA, B.data_ptr(), ldb, psB,
+                       _abi.q4(beta), C.data_ptr(), ldc, psC, _abi.LAYOUT[layout],
+                       _abi.PRECISION[prec], wptr, wbytes, _stream_handle(stream))
+    _abi.check(rc, "qgemm_mixed")
+    return C
+
+
 def qtrmm(side, uplo, trans, diag, m, n, alpha, A, B, C, layout="interleaved", ws=None,
           stream=None, precision=None):
     """Triangular product into C (written, not read, must not be B):

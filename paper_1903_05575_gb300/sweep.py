@@ -11,6 +11,8 @@ N x N products, Sec. 5), printing one JSON line per case:
          m = n = k in --sliced-sizes, the --ops pairs, both layouts.
   trmm:  qtrmm (left, lower, op N) at --trmm sizes on every precision, with
          its time relative to the GEMM of the same size.
+  mixed: qgemm_mixed with complex / real factors at --mixed sizes on the
+         tensor-core precisions.
 
 Timing: CUDA events on the launching stream around `reps` calls after
 warm-up; inputs of every case are larger than L2 except the smallest FP64
@@ -157,6 +159,28 @@ def trmm_case(n, precision, reps):
             "tflops_trmm_work": 16.0 * n ** 3 / (tr * 1e-3) / 1e12, "rel_err_sampled": err}
 
 
+def mixed_case(n, precision, types, reps):
+    """qgemm_mixed at m = n = k = n, op N,N, alpha = 1, beta = 0: time of the
+    mixed product and of the quaternion product on the same precision."""
+    import torch
+
+    from . import ops
+    dev = torch.device("cuda", torch.cuda.current_device())
+    dt = torch.float32 if precision == "split_bf16" else torch.float64
+    width = {"H": 4, "C": 2, "R": 1}
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7 * n)
+    A = torch.randn((n, n, width[types[0]]), dtype=dt, device=dev, generator=gen)
+    B = torch.randn((n, n, width[types[1]]), dtype=dt, device=dev, generator=gen)
+    C = torch.zeros((n, n, 4), dtype=dt, device=dev)
+    p = None if precision == "split_bf16" else precision
+    one, zero = (1.0, 0, 0, 0), (0.0, 0, 0, 0)
+    ms = _timed(lambda: ops.qgemm_mixed(types[0], types[1], "N", "N", n, n, n, one, A, B, zero,
+                                        C, precision=p), reps)
+    return {"path": "mixed_" + precision, "types": types, "n": n, "ms": ms,
+            "real_flops": {"HH": 32, "HC": 16, "CH": 16, "HR": 8, "RH": 8}.get(types, 0) * n ** 3}
+
+
 def complex_comparison(n, reps, qgemm_ms=None):
     """The paper's experiment (Sec. 5, Fig. 4) on this GPU: the same product
     through cuBLAS ZGEMM on the 2n x 2n complex representation (Eq. qmat_complex,
@@ -203,6 +227,7 @@ def main():
     ap.add_argument("--split-sizes", default="2048,8192")
     ap.add_argument("--sliced-sizes", default="")
     ap.add_argument("--trmm", default="", help="sizes for the triangular product")
+    ap.add_argument("--mixed", default="", help="sizes for the mixed-type products")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--compare", default="", help="sizes for the cuBLAS ZGEMM/DGEMM comparison")
     a = ap.parse_args()
@@ -233,6 +258,10 @@ def main():
     for n in [int(x) for x in a.trmm.split(",") if x]:
         for prec in ("fp64", "fp64_sliced", "split_bf16"):
             print(json.dumps(trmm_case(n, prec, 2 if prec == "fp64" else 5)), flush=True)
+    for n in [int(x) for x in a.mixed.split(",") if x]:
+        for prec in ("fp64_sliced", "split_bf16"):
+            for types in ("HH", "HC", "CH", "HR", "RH"):
+                print(json.dumps(mixed_case(n, prec, types, 5)), flush=True)
     for n in [int(x) for x in a.compare.split(",") if x]:
         print(json.dumps(complex_comparison(n, a.reps)), flush=True)
 
