@@ -55,10 +55,10 @@ def oracle_loss(Xs, Ws, mb, k, n):
     return float(np.sum(Y * Y))
 
 
-def gpu_grads(Xs, Ws, dtype):
+def gpu_grads(Xs, Ws, dtype, precision=None):
     X = to_dev(Xs, dtype).requires_grad_(True)
     W = to_dev(Ws, dtype).requires_grad_(True)
-    Y = QLinearFunction.apply(X, W)
+    Y = QLinearFunction.apply(X, W, "interleaved", precision)
     L = (Y.double() * Y.double()).sum()
     L.backward()
     return X.grad.double().cpu().numpy(), W.grad.double().cpu().numpy(), float(L)
@@ -91,14 +91,16 @@ def test_grad_vs_finite_differences_fp64():
         assert rel_fro(got, fd) <= 1e-9, rel_fro(got, fd)
 
 
-@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 2e-6)])
-def test_grad_vs_real_block_form(dtype, tol):
+@pytest.mark.parametrize("dtype,tol,precision", [(torch.float64, 1e-12, None),
+                                                 (torch.float32, 2e-6, None),
+                                                 (torch.float64, 1e-12, "fp64_sliced")])
+def test_grad_vs_real_block_form(dtype, tol, precision):
     mb, k, n = 70, 40, 36
     Xs = qsynth.normal(mb, k, 61)
     Ws = qsynth.normal(k, n, 62, scale=1.0 / 16)
     if dtype == torch.float32:
         Xs, Ws = Xs.astype(np.float32).astype(np.float64), Ws.astype(np.float32).astype(np.float64)
-    gX, gW, L = gpu_grads(Xs, Ws, dtype)
+    gX, gW, L = gpu_grads(Xs, Ws, dtype, precision)
     rX, rW, Lr = real_block_loss_grads(qsynth.components(Xs, mb, "interleaved"),
                                        qsynth.components(Ws, k, "interleaved"))
     assert abs(L - Lr) <= 10 * tol * Lr
