@@ -333,11 +333,10 @@ size_t qtrmm_workspace_bytes(int side, int uplo, int transA, int diag, int64_t m
  * of (r, c) at w*(r + c*ld) + s, w = 2 or 1), split planes 2 or 1 planes at
  * the plane stride.  op conjugates as in H (conj(z) = z^0 - z^1 e1).
  * Arguments: 1 typeA, 2 typeB, then the arguments of qgemm() as 3..23
- * (opA = 3 ... stream = 23) for the -i return.  On the tensor-core
- * precisions a complex (real) factor halves (quarters) the MMAs of the
- * quaternion product; the FP64 path runs the quaternion product on a
- * quaternion copy of the narrow operands.  Workspace from
- * qgemm_mixed_workspace_bytes() (also for QGEMM_FP64 with a narrow operand).
+ * (opA = 3 ... stream = 23) for the -i return.  A complex (real) factor
+ * halves (quarters) the tensor-core or DMMA work of the quaternion product
+ * (when both factors are narrow, the FP64 path copies the left one as a
+ * quaternion matrix).  Workspace from qgemm_mixed_workspace_bytes().
  */
 int qgemm_mixed(int typeA, int typeB, int opA, int opB, int64_t m, int64_t n, int64_t k,
                 const double alpha[4],

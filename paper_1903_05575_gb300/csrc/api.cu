@@ -323,11 +323,13 @@ int qgemm_get_last_device_error(void) {
   int e3 = grouped_take_device_error();
   int e4 = misc_take_device_error();
   int e5 = sliced_take_device_error();
+  int e6 = fp64m_take_device_error();
   if (e) return e;
   if (e2) return e2;
   if (e3) return e3;
   if (e4) return e4;
-  return e5;
+  if (e5) return e5;
+  return e6;
 }
 
 const char *qgemm_status_string(int status) {

@@ -201,6 +201,7 @@ fp64::Operands fp64_operands(const GemmDesc &d) {
   a.beta_zero = d.beta_zero ? 1 : 0;
   a.tri = d.tri;
   a.krange = d.krange;
+  a.swap = d.swap;
   return a;
 }
 

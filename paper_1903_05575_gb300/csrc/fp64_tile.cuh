@@ -43,6 +43,7 @@ struct Operands {
   int tmaA, tmaB, beta_zero;
   int tri;  // 0 full; 1 lower (row >= col) only; 2 upper; diagonal written real
   int krange;  // k-range of a tile when op(A) or op(B) is triangular (see GemmDesc)
+  int swap;    // 1: the tile holds D = (op(A) op(B))^H; store C = conj(D)^T
 };
 
 // True when the tile at quaternion offset (i0, n0) of size BMQ x BNQ has no
@@ -54,22 +55,23 @@ __device__ __forceinline__ bool tile_outside(int tri, int64_t i0, int64_t n0, in
 }
 
 // Shared-memory index of component s of stored element (r, c) of a tile with
-// R stored rows and CC stored columns (the TMA box order).
-template <int LAYOUT, int R, int CC>
+// R stored rows and CC stored columns (the TMA box order); W components per
+// element (4 quaternion, 2 complex, 1 real).
+template <int LAYOUT, int R, int CC, int W = 4>
 __device__ __forceinline__ int tile_idx(int r, int c, int s) {
-  if (LAYOUT == QGEMM_INTERLEAVED) return s + 4 * (r + R * c);
+  if (LAYOUT == QGEMM_INTERLEAVED) return s + W * (r + R * c);
   return r + R * (c + CC * s);
 }
 
-template <int LAYOUT, int R, int CC>
+template <int LAYOUT, int R, int CC, int W = 4>
 __device__ void load_tile_plain(double *dst, const double *base, int64_t rows, int64_t cols,
                                 int64_t ld, int64_t ps, int64_t r0, int64_t c0) {
-  constexpr int N = R * CC * 4;
+  constexpr int N = R * CC * W;
   for (int e = threadIdx.x; e < N; e += kThreads) {
     int r, c, s;
     if (LAYOUT == QGEMM_INTERLEAVED) {
-      s = e & 3;
-      const int rest = e >> 2;
+      s = e % W;
+      const int rest = e / W;
       r = rest % R;
       c = rest / R;
     } else {
@@ -80,7 +82,7 @@ __device__ void load_tile_plain(double *dst, const double *base, int64_t rows, i
     const int64_t gr = r0 + r, gc = c0 + c;
     double v = 0.0;
     if (gr < rows && gc < cols)
-      v = LAYOUT == QGEMM_INTERLEAVED ? base[4 * (gr + gc * ld) + s] : base[s * ps + gr + gc * ld];
+      v = LAYOUT == QGEMM_INTERLEAVED ? base[W * (gr + gc * ld) + s] : base[s * ps + gr + gc * ld];
     dst[e] = v;
   }
 }
@@ -105,7 +107,11 @@ __device__ __forceinline__ void tma_box(double *dst, const CUtensorMap *map, uin
 // kb_run counts k-blocks consumed by this CTA so far (ring slot and barrier
 // phase).  Returns false if a bounded wait gave up (after draining its own
 // copies); the caller then stops.
-template <int LAYOUT, bool TA, bool TB, int BMQ, int BNQ>
+// WB: components of op(B)'s elements (4; 2 or 1 for a complex or real right
+// factor, loaded with plain loads).  Then b^j = 0 for j >= WB, and one DMMA's
+// k = 4 spans 4 / WB values of kappa: lane k-index t is kappa offset t / WB,
+// component j = t % WB, and L(a)[c][j] is gathered for that (kappa, j).
+template <int LAYOUT, bool TA, bool TB, int BMQ, int BNQ, int WB = 4>
 __device__ bool tile(const Operands &p, const CUtensorMap *tmA, const CUtensorMap *tmB,
                      double *sA, double *sB, uint64_t *full, uint32_t &kb_run, int64_t i0,
                      int64_t n0, uint64_t limit_ns, int *err_word) {
@@ -181,8 +187,8 @@ __device__ bool tile(const Operands &p, const CUtensorMap *tmA, const CUtensorMa
       load_tile_plain<LAYOUT, A_R, A_C>(a_t, p.A, p.a_rows, p.a_cols, p.lda, p.psA,
                                         TA ? kk0 : i0, TA ? i0 : kk0);
     if (!p.tmaB)
-      load_tile_plain<LAYOUT, B_R, B_C>(b_t, p.B, p.b_rows, p.b_cols, p.ldb, p.psB,
-                                        TB ? n0 : kk0, TB ? kk0 : n0);
+      load_tile_plain<LAYOUT, B_R, B_C, WB>(b_t, p.B, p.b_rows, p.b_cols, p.ldb, p.psB,
+                                            TB ? n0 : kk0, TB ? kk0 : n0);
     const bool ok = mbar_wait_bounded(&full[st], par, limit_ns);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
@@ -195,29 +201,67 @@ __device__ bool tile(const Operands &p, const CUtensorMap *tmA, const CUtensorMa
       return false;
     }
     const int kk_end = static_cast<int>(min(static_cast<int64_t>(kBKQ), p.k - kk0));
+    if (WB == 4) {
 #pragma unroll 4
-    for (int kk = 0; kk < kk_end; ++kk) {
-      double a[2][2], b[NC];
+      for (int kk = 0; kk < kk_end; ++kk) {
+        double a[2][2], b[NC];
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const int i = arow + 4 * r;
-        a[r][0] = flip_sign(a_t[TA ? tile_idx<LAYOUT, A_R, A_C>(kk, i, compA)
-                                   : tile_idx<LAYOUT, A_R, A_C>(i, kk, compA)], negA);
-        a[r][1] = flip_sign(a_t[TA ? tile_idx<LAYOUT, A_R, A_C>(kk, i + 2, compA)
-                                   : tile_idx<LAYOUT, A_R, A_C>(i + 2, kk, compA)], negA);
-      }
-#pragma unroll
-      for (int cc = 0; cc < NC; ++cc) {
-        const int j = bcol + 8 * cc;
-        b[cc] = b_t[TB ? tile_idx<LAYOUT, B_R, B_C>(j, kk, t) : tile_idx<LAYOUT, B_R, B_C>(kk, j, t)];
-      }
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        if (!row_live[r]) continue;
+        for (int r = 0; r < 2; ++r) {
+          const int i = arow + 4 * r;
+          a[r][0] = flip_sign(a_t[TA ? tile_idx<LAYOUT, A_R, A_C>(kk, i, compA)
+                                     : tile_idx<LAYOUT, A_R, A_C>(i, kk, compA)], negA);
+          a[r][1] = flip_sign(a_t[TA ? tile_idx<LAYOUT, A_R, A_C>(kk, i + 2, compA)
+                                     : tile_idx<LAYOUT, A_R, A_C>(i + 2, kk, compA)], negA);
+        }
 #pragma unroll
         for (int cc = 0; cc < NC; ++cc) {
-          if (!col_live[cc]) continue;
-          dmma_16x8x4(acc[r][cc], a[r][0], a[r][1], b[cc]);
+          const int j = bcol + 8 * cc;
+          b[cc] = b_t[TB ? tile_idx<LAYOUT, B_R, B_C>(j, kk, t) : tile_idx<LAYOUT, B_R, B_C>(kk, j, t)];
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          if (!row_live[r]) continue;
+#pragma unroll
+          for (int cc = 0; cc < NC; ++cc) {
+            if (!col_live[cc]) continue;
+            dmma_16x8x4(acc[r][cc], a[r][0], a[r][1], b[cc]);
+          }
+        }
+      }
+    } else {
+      // narrow right factor: this lane's (kappa offset, component j) per step;
+      // steps past k read the zero fill of the tiles
+      constexpr int KPS = 4 / WB;
+      const int jw = t % WB, kofs = t / WB;
+      const int compW = c_lane ^ jw;
+      const uint32_t negW = ((p.negmask >> (4 * c_lane + jw)) & 1u) << 31;
+      const int nsteps = (kk_end + KPS - 1) / KPS;
+#pragma unroll 2
+      for (int stp = 0; stp < nsteps; ++stp) {
+        const int kk = stp * KPS + kofs;
+        double a[2][2], b[NC];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int i = arow + 4 * r;
+          a[r][0] = flip_sign(a_t[TA ? tile_idx<LAYOUT, A_R, A_C>(kk, i, compW)
+                                     : tile_idx<LAYOUT, A_R, A_C>(i, kk, compW)], negW);
+          a[r][1] = flip_sign(a_t[TA ? tile_idx<LAYOUT, A_R, A_C>(kk, i + 2, compW)
+                                     : tile_idx<LAYOUT, A_R, A_C>(i + 2, kk, compW)], negW);
+        }
+#pragma unroll
+        for (int cc = 0; cc < NC; ++cc) {
+          const int j = bcol + 8 * cc;
+          b[cc] = b_t[TB ? tile_idx<LAYOUT, B_R, B_C, WB>(j, kk, jw)
+                         : tile_idx<LAYOUT, B_R, B_C, WB>(kk, j, jw)];
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          if (!row_live[r]) continue;
+#pragma unroll
+          for (int cc = 0; cc < NC; ++cc) {
+            if (!col_live[cc]) continue;
+            dmma_16x8x4(acc[r][cc], a[r][0], a[r][1], b[cc]);
+          }
         }
       }
     }
@@ -249,12 +293,21 @@ __device__ bool tile(const Operands &p, const CUtensorMap *tmA, const CUtensorMa
         double P[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) P[j] = __shfl_sync(0xffffffffu, acc[r][cc][e], src_base | (j << 2));
+        // a turned-around problem holds D = (op(A) op(B))^H: C = conj(D)^T
+        int64_t ci = qi, cj = qn;
+        if (p.swap) {
+          ci = qn;
+          cj = qi;
+          P[1] = -P[1];
+          P[2] = -P[2];
+          P[3] = -P[3];
+        }
         double out = la[0] * P[0];
         out = fma(la[1], P[1], out);
         out = fma(la[2], P[2], out);
         out = fma(la[3], P[3], out);
-        double *dst = LAYOUT == QGEMM_INTERLEAVED ? p.C + 4 * (qi + qn * p.ldc) + c_lane
-                                                  : p.C + c_lane * p.psC + qi + qn * p.ldc;
+        double *dst = LAYOUT == QGEMM_INTERLEAVED ? p.C + 4 * (ci + cj * p.ldc) + c_lane
+                                                  : p.C + c_lane * p.psC + ci + cj * p.ldc;
         if (!p.beta_zero) {
           const double cin = inb ? *dst : 0.0;
           double Cq[4];

@@ -71,6 +71,7 @@ inline bool precision_fp64_data(int p) { return p != QGEMM_FP32_SPLIT_BF16; }
 
 // Launchers (return QGEMM status codes).
 int launch_fp64_gemm(const GemmDesc &d, cudaStream_t stream);
+int launch_fp64_mixed(const GemmDesc &d, cudaStream_t stream);
 int launch_scale(const GemmDesc &d, bool fp64, cudaStream_t stream);
 int launch_herk_scale(const GemmDesc &d, bool fp64, cudaStream_t stream);
 int split_workspace_bytes(const GemmDesc &d, size_t *bytes);
@@ -89,6 +90,7 @@ int split_take_device_error();
 int grouped_take_device_error();
 int misc_take_device_error();
 int sliced_take_device_error();
+int fp64m_take_device_error();
 int debug_unsatisfied_wait(uint64_t limit_ns, cudaStream_t stream);
 int probe_peak(int which, double seconds, double *tflops, cudaStream_t stream);
 

@@ -10,8 +10,10 @@
 // quaternion product.  A quaternion left factor with a narrow right factor
 // is turned around with (AB)^H = B^H A^H (Sec. 2.2): the kernel computes
 // D = op(B)^H op(A)^H with the narrow factor on the left and stores
-// C = conj(D)^T.  The FP64 path writes the narrow operands as quaternion
-// matrices into the workspace and runs the quaternion product.
+// C = conj(D)^T.  The FP64 DMMA path takes the narrow factor on the RIGHT
+// (fp64_mixed.cu: one DMMA spans 4 / width values of kappa), turning a
+// narrow left factor around the same way; when both are narrow the left one
+// is copied as a quaternion matrix into the workspace.
 #include <cstring>
 
 #include "common.cuh"
@@ -84,20 +86,29 @@ int mixed_desc(int typeA, int typeB, int opA, int opB, int64_t m, int64_t n, int
   if (rc) return rc - 2;  // qgemm position i is argument i + 2 here
   d->A.width = kWidth[typeA];
   d->B.width = kWidth[typeB];
-  if (precision == QGEMM_FP64 || d->k == 0) return 0;
+  if (d->k == 0) return 0;
+  auto turn_around = [](GemmDesc *x) {
+    GemmDesc t = *x;
+    t.m = x->n;
+    t.n = x->m;
+    t.opA = op_conjtrans(x->opB);
+    t.opB = op_conjtrans(x->opA);
+    t.A = x->B;
+    t.B = x->A;
+    t.swap = 1;
+    *x = t;
+  };
+  if (precision == QGEMM_FP64) {
+    // the narrow factor on the right (both narrow: the left one is copied)
+    if (typeA != 0 && typeB == 0) turn_around(d);
+    return 0;
+  }
+  // tensor-core precisions: the narrow factor on the left
   if (typeA != 0) {
     d->kwidth = kWidth[typeA];
   } else if (typeB != 0) {
-    GemmDesc t = *d;
-    t.m = d->n;
-    t.n = d->m;
-    t.opA = op_conjtrans(d->opB);
-    t.opB = op_conjtrans(d->opA);
-    t.A = d->B;
-    t.B = d->A;
-    t.kwidth = kWidth[typeB];
-    t.swap = 1;
-    *d = t;
+    turn_around(d);
+    d->kwidth = kWidth[typeB];
   }
   return 0;
 }
@@ -123,7 +134,7 @@ size_t qgemm_mixed_workspace_bytes(int typeA, int typeB, int opA, int opB, int64
                  planes ? ra * ca : 0, reinterpret_cast<const void *>(p), rb, planes ? rb * cb : 0,
                  one, reinterpret_cast<void *>(p), m, planes ? m * n : 0, layout, precision, &d))
     return 0;
-  if (precision == QGEMM_FP64) return embed_bytes(d.A) + embed_bytes(d.B);
+  if (precision == QGEMM_FP64) return embed_bytes(d.A);
   size_t g = 0;
   if (precision == QGEMM_FP32_SPLIT_BF16 && split_workspace_bytes(d, &g)) return 0;
   if (precision == QGEMM_FP64_SLICED_BF16 && sliced_workspace_bytes(d, &g)) return 0;
@@ -152,20 +163,16 @@ int qgemm_mixed(int typeA, int typeB, int opA, int opB, int64_t m, int64_t n, in
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (d.k == 0) return launch_scale(d, precision_fp64_data(precision), s);
   if (precision == QGEMM_FP64) {
-    unsigned char *ws = static_cast<unsigned char *>(workspace);
-    size_t off = 0;
-    for (MatView *v : {&d.A, &d.B}) {
-      if (v->width == 4) continue;
-      double *Q = reinterpret_cast<double *>(ws + off);
-      rc = launch_embed(*v, layout, Q, s);
+    if (d.A.width != 4) {  // both factors narrow: the left one as a quaternion matrix
+      double *Q = static_cast<double *>(workspace);
+      rc = launch_embed(d.A, layout, Q, s);
       if (rc) return rc;
-      off += embed_bytes(*v);
-      v->ptr = Q;
-      v->ld = v->rows > 0 ? v->rows : 1;
-      v->ps = v->rows * v->cols;
-      v->width = 4;
+      d.A.ptr = Q;
+      d.A.ld = d.A.rows > 0 ? d.A.rows : 1;
+      d.A.ps = d.A.rows * d.A.cols;
+      d.A.width = 4;
     }
-    return launch_fp64_gemm(d, s);
+    return d.B.width == 4 ? launch_fp64_gemm(d, s) : launch_fp64_mixed(d, s);
   }
   if (precision == QGEMM_FP64_SLICED_BF16)
     return launch_sliced_gemm(d, workspace, workspace_bytes, s);
