@@ -228,6 +228,7 @@ def main():
     ap.add_argument("--sliced-sizes", default="")
     ap.add_argument("--trmm", default="", help="sizes for the triangular product")
     ap.add_argument("--mixed", default="", help="sizes for the mixed-type products")
+    ap.add_argument("--mixed-fp64", default="", help="sizes for the FP64 mixed-type products")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--compare", default="", help="sizes for the cuBLAS ZGEMM/DGEMM comparison")
     a = ap.parse_args()
@@ -262,6 +263,9 @@ def main():
         for prec in ("fp64_sliced", "split_bf16"):
             for types in ("HH", "HC", "CH", "HR", "RH"):
                 print(json.dumps(mixed_case(n, prec, types, 5)), flush=True)
+    for n in [int(x) for x in a.mixed_fp64.split(",") if x]:
+        for types in ("HH", "HC", "CH", "HR", "RH"):
+            print(json.dumps(mixed_case(n, "fp64", types, 2)), flush=True)
     for n in [int(x) for x in a.compare.split(",") if x]:
         print(json.dumps(complex_comparison(n, a.reps)), flush=True)
 
