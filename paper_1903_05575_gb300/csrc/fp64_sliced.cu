@@ -788,14 +788,15 @@ __device__ __forceinline__ void digits6(long long X, int (&d)[NSL]) {
 //   A: A'_t[r][4 kappa + j] = d_t(a^j)
 //   B: B'_t[4 r + c][4 kappa + j] = sign(j, j^c) d_t(b^(j^c))
 // Columns kappa >= kq up to kp/4 are zeros (K padding).
-// The first kw of four BF16 values at dst (aligned to kw values).
-__device__ __forceinline__ void store_kw(__nv_bfloat16 *dst, const __nv_bfloat16 (&w)[4], int kw) {
+// The first kw of four BF16 values (bits lo = v0 | v1 << 16, hi = v2 | v3 << 16)
+// at dst (aligned to kw values).
+__device__ __forceinline__ void store_bits(__nv_bfloat16 *dst, uint32_t lo, uint32_t hi, int kw) {
   if (kw == 4)
-    *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(w);
+    *reinterpret_cast<uint2 *>(dst) = make_uint2(lo, hi);
   else if (kw == 2)
-    *reinterpret_cast<uint32_t *>(dst) = *reinterpret_cast<const uint32_t *>(w);
+    *reinterpret_cast<uint32_t *>(dst) = lo;
   else
-    dst[0] = w[0];
+    *reinterpret_cast<unsigned short *>(dst) = static_cast<unsigned short>(lo & 0xffffu);
 }
 
 struct SliceSmem {
@@ -831,10 +832,14 @@ __device__ __forceinline__ void slice_tile(const SliceArgs &p, int64_t rt, int64
       double e4[4] = {0.0, 0.0, 0.0, 0.0};
       if (p.layout == QGEMM_INTERLEAVED) {
         const double *e = p.X + p.width * (sr + sc * p.ld);
-        for (int q = 0; q < p.width; ++q) e4[q] = e[q];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < p.width) e4[q] = e[q];
       } else {
         const double *e = p.X + sr + sc * p.ld;
-        for (int q = 0; q < p.width; ++q) e4[q] = e[q * p.ps];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < p.width) e4[q] = e[q * p.ps];
       }
       v = make_double4(e4[0], e4[1], e4[2], e4[3]);
       if (p.negmask & 2u) v.y = -v.y;
@@ -856,29 +861,30 @@ __device__ __forceinline__ void slice_tile(const SliceArgs &p, int64_t rt, int64
 #pragma unroll
     for (int j = 0; j < 4; ++j)  // a non-finite row gets digits 0 (its C entries NaN)
       digits6(sft == kNonFinite ? 0ll : round_scaled(comp[j], sft), d[j]);
+    // BF16 bits of each digit (exact: |d| <= 256); a sign flip is an XOR
+    uint32_t hb[4][NSL];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int t = 0; t < NSL; ++t) hb[j][t] = __float_as_uint(static_cast<float>(d[j][t])) >> 16;
     if (!IS_B) {
 #pragma unroll
-      for (int t = 0; t < NSL; ++t) {
-        __nv_bfloat16 *dst = p.out + t * p.slice_stride + r * p.kp + p.kw * kq;
-        __align__(8) __nv_bfloat16 w[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) w[j] = __float2bfloat16_rn(static_cast<float>(d[j][t]));
-        store_kw(dst, w, p.kw);
-      }
+      for (int t = 0; t < NSL; ++t)
+        store_bits(p.out + t * p.slice_stride + r * p.kp + p.kw * kq, hb[0][t] | (hb[1][t] << 16),
+                   hb[2][t] | (hb[3][t] << 16), p.kw);
     } else {
 #pragma unroll
       for (int t = 0; t < NSL; ++t)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          __align__(8) __nv_bfloat16 w[4];
+          uint32_t v[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const int q = j ^ c;
-            const int x = basis_sign(j, q) < 0 ? -d[q][t] : d[q][t];
-            w[j] = __float2bfloat16_rn(static_cast<float>(x));
+            v[j] = hb[q][t] ^ (basis_sign(j, q) < 0 ? 0x8000u : 0u);
           }
-          __nv_bfloat16 *dst = p.out + t * p.slice_stride + (4 * r + c) * p.kp + p.kw * kq;
-          store_kw(dst, w, p.kw);
+          store_bits(p.out + t * p.slice_stride + (4 * r + c) * p.kp + p.kw * kq,
+                     v[0] | (v[1] << 16), v[2] | (v[3] << 16), p.kw);
         }
     }
   }

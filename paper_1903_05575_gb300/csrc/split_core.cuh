@@ -186,14 +186,14 @@ __device__ __forceinline__ float4 load_elem(const PrepArgs &p, int64_t sr, int64
   float v[4] = {0.f, 0.f, 0.f, 0.f};
   if (p.layout == QGEMM_INTERLEAVED) {
     const float *e = p.X + p.width * (sr + sc * p.ld);
-    if (p.width == 4) {
-      v[0] = e[0]; v[1] = e[1]; v[2] = e[2]; v[3] = e[3];
-    } else {
-      for (int s = 0; s < p.width; ++s) v[s] = e[s];
-    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+      if (s < p.width) v[s] = e[s];
   } else {
     const float *e = p.X + sr + sc * p.ld;
-    for (int s = 0; s < p.width; ++s) v[s] = e[s * p.ps];
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+      if (s < p.width) v[s] = e[s * p.ps];
   }
   return make_float4(v[0], v[1], v[2], v[3]);
 }
