@@ -133,8 +133,9 @@ struct Ctl {
   uint64_t full[SST];
   uint64_t empty[SST];
   uint64_t accfull;  // the MMAs of a chunk completed
-  uint64_t free23;   // drain has read levels 2, 3 (and 4, 5 after a tile's last chunk)
-  uint64_t free01;   // drain has read levels 0, 1
+  uint64_t free23;   // drain has read levels 2, 3 of a chunk
+  uint64_t free01;   // drain has read levels 0, 1 of a chunk
+  uint64_t free45;   // drain has read levels 4, 5 of a tile
   uint64_t done;
   uint32_t tmem_base;
   int abort;
@@ -220,6 +221,27 @@ __device__ __forceinline__ void mma_levels01(uint32_t d, uint32_t ka, uint32_t k
                                              bool chunk_start) {
   mma(d, ka, kb, 2 * SBN, chunk_start ? 0u : 1u);                         // 00 01
   mma(d + SBN, ka + kSliceA, kb, 1 * SBN, 1u);                            // 10
+}
+
+// The same 21 products in three groups by level, for the first stage of a
+// chunk: levels 4, 5 (11 products, 6 MMAs) do not wait for the drain of the
+// previous chunk, levels 2, 3 (7 products, 4 MMAs) and 0, 1 (3 products, 2
+// MMAs) wait for their regions to be read.
+__device__ __forceinline__ void mma_levels45(uint32_t d, uint32_t ka, uint32_t kb,
+                                             bool tile_start) {
+  mma(d + 4 * SBN, ka, kb + 4 * kSliceB, 2 * SBN, tile_start ? 0u : 1u);  // 04 05
+  mma(d + 4 * SBN, ka + 1 * kSliceA, kb + 3 * kSliceB, 2 * SBN, 1u);      // 13 14
+  mma(d + 4 * SBN, ka + 2 * kSliceA, kb + 2 * kSliceB, 2 * SBN, 1u);      // 22 23
+  mma(d + 4 * SBN, ka + 3 * kSliceA, kb + 1 * kSliceB, 2 * SBN, 1u);      // 31 32
+  mma(d + 4 * SBN, ka + 4 * kSliceA, kb, 2 * SBN, 1u);                    // 40 41
+  mma(d + 5 * SBN, ka + 5 * kSliceA, kb, 1 * SBN, 1u);                    // 50
+}
+__device__ __forceinline__ void mma_levels23(uint32_t d, uint32_t ka, uint32_t kb,
+                                             bool chunk_start) {
+  mma(d + 2 * SBN, ka, kb + 2 * kSliceB, 2 * SBN, chunk_start ? 0u : 1u);  // 02 03
+  mma(d + 2 * SBN, ka + 1 * kSliceA, kb + 1 * kSliceB, 2 * SBN, 1u);       // 11 12
+  mma(d + 2 * SBN, ka + 2 * kSliceA, kb, 2 * SBN, 1u);                     // 20 21
+  mma(d + 3 * SBN, ka + 3 * kSliceA, kb, 1 * SBN, 1u);                     // 30
 }
 
 // TMEM <-> registers, 32x32b shapes (lane = row of this thread).
@@ -432,6 +454,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
     mbar_init(&ctl->accfull, 1);
     mbar_init(&ctl->free23, kDrainWarps);
     mbar_init(&ctl->free01, kDrainWarps);
+    mbar_init(&ctl->free45, kDrainWarps);
     mbar_init(&ctl->done, 1);
     ctl->abort = 0;
     fence_barrier_init();
@@ -479,12 +502,14 @@ __global__ void __launch_bounds__(kSThreads, 1)
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
-    // A chunk starts once the drain has read levels 2..5 of the previous one;
-    // its first stage issues the level 2..5 products of both k-steps, then
-    // waits until levels 0, 1 are read too.
+    // The first stage of a chunk issues the level 4, 5 products of both
+    // k-steps at once (those regions are read only at a tile's end: a tile's
+    // first chunk waits for that), then the level 2, 3 products once the
+    // drain has read those regions of the previous chunk, then levels 0, 1.
+    // The other stages issue all 21 products as 8 MMAs.
     if (elect_one()) {
       const uint32_t ring_addr = smem_u32(ring);
-      uint32_t s_run = 0, c_run = 0;
+      uint32_t s_run = 0, c_run = 0, t_run = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const SlicedParams *g;
@@ -495,14 +520,18 @@ __global__ void __launch_bounds__(kSThreads, 1)
         int kb_lo, kb_hi;
         kb_range(*g, mt, nt, kb_lo, kb_hi);
         const int nch = (kb_hi - kb_lo + kChunkKb - 1) / kChunkKb;
-        for (int ch = 0; ch < nch && ok; ++ch, ++c_run) {
-          const uint32_t par = (c_run & 1) ^ 1;
-          if (!wait_phase(&ctl->free23, par, limit_ns, ctl)) {
+        if (nch > 0) {
+          // levels 4, 5 of the previous tile read
+          if (!wait_phase(&ctl->free45, (t_run & 1) ^ 1, limit_ns, ctl)) {
             set_abort(ctl);
             ok = false;
             break;
           }
+          ++t_run;
           tc_fence_after();
+        }
+        for (int ch = 0; ch < nch && ok; ++ch, ++c_run) {
+          const uint32_t par = (c_run & 1) ^ 1;
           const int kb0 = kb_lo + ch * kChunkKb, kb1 = min(kb_hi, kb0 + kChunkKb);
           for (int kb = kb0; kb < kb1; ++kb, ++s_run) {
             const int st = s_run % SST;
@@ -517,7 +546,16 @@ __global__ void __launch_bounds__(kSThreads, 1)
             if (kb == kb0) {
 #pragma unroll
               for (int ks = 0; ks < SBK / 16; ++ks)
-                mma_levels25(tmem, sa + ks * 32, sb + ks * 32, ks == 0, ks == 0 && ch == 0);
+                mma_levels45(tmem, sa + ks * 32, sb + ks * 32, ks == 0 && ch == 0);
+              if (!wait_phase(&ctl->free23, par, limit_ns, ctl)) {
+                set_abort(ctl);
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+#pragma unroll
+              for (int ks = 0; ks < SBK / 16; ++ks)
+                mma_levels23(tmem, sa + ks * 32, sb + ks * 32, ks == 0);
               if (!wait_phase(&ctl->free01, par, limit_ns, ctl)) {
                 set_abort(ctl);
                 ok = false;
@@ -623,6 +661,9 @@ __global__ void __launch_bounds__(kSThreads, 1)
           for (int q = 0; q < 16; ++q)
             tail[16 * h + q] = fmaf(v5[q], 0.00390625f, v4[q]) * 0.00390625f;
         }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ctl->free45);
         float v[32];
         tmem_ld32(base + 2 * SBN, v);
         add_level<8>(T, v);
