@@ -402,6 +402,7 @@ int qgemm_debug_unsatisfied_wait(uint64_t limit_ns, void *stream);
  *     zero operands
  *   4, 5, 6 the same instruction at N = 256, 128, 64 on operands holding
  *     integers in [-127, 127]
+ *   7 DMMA and DFMA together (alternate warps): whether the two FP64 pipes add
  * Runs for roughly `seconds` and writes the achieved TFLOP/s (2 per FMA).
  */
 int qgemm_probe_peak(int which, double seconds, double *tflops, void *stream);

@@ -352,7 +352,7 @@ int qgemm_debug_unsatisfied_wait(uint64_t limit_ns, void *stream) {
 }
 
 int qgemm_probe_peak(int which, double seconds, double *tflops, void *stream) {
-  if (which < 0 || which > 6) return -1;
+  if (which < 0 || which > 7) return -1;
   if (!(seconds > 0.0) || seconds > 60.0) return -2;
   if (tflops == nullptr) return -3;
   int rc = device_ready();

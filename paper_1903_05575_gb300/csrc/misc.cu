@@ -34,10 +34,14 @@ __global__ void probe_kernel(int iters, double seed) {
   for (int c = 0; c < NC; ++c)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[c][j] = 0.0;
-  for (int it = 0; it < iters; ++it) {
+  // KIND 2: even warps run the DMMA chains, odd warps 8x as many DFMA
+  // iterations (about the same time alone): do the two pipes add up?
+  const bool dmma = KIND == 0 || (KIND == 2 && ((threadIdx.x >> 5) & 1) == 0);
+  const int n_it = (KIND == 2 && !dmma) ? 8 * iters : iters;
+  for (int it = 0; it < n_it; ++it) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      if (KIND == 0) {
+      if (dmma) {
         asm volatile(
             "mma.sync.aligned.m16n8k4.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, {%4,%5}, {%6}, "
             "{%0,%1,%2,%3};\n"
@@ -92,21 +96,23 @@ int misc_take_device_error() {
 }
 
 int probe_peak(int which, double seconds, double *tflops, cudaStream_t stream) {
-  if (which >= 3) return probe_tcgen05_bf16(which, seconds, tflops, stream);
+  if (which >= 3 && which <= 6) return probe_tcgen05_bf16(which, seconds, tflops, stream);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int blocks = sms * 2, threads = which == 2 ? 512 : 256;
+  const int blocks = sms * 2, threads = (which == 2 || which == 7) ? 512 : 256;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   double flops_per_iter_thread;
   if (which == 0) flops_per_iter_thread = 2.0 * 16 * 8 * 4 * 8 / 32.0;  // 8 DMMA per warp-iter
   else if (which == 1) flops_per_iter_thread = 2.0 * 2 * 8;
+  else if (which == 7) flops_per_iter_thread = 0.5 * (2.0 * 16 * 8 * 4 * 8 / 32.0) + 0.5 * 8 * 32;
   else flops_per_iter_thread = 2.0 * 16;
   auto launch = [&](int iters) {
     if (which == 0) probe_kernel<0><<<blocks, threads, 0, stream>>>(iters, 1.0);
     else if (which == 1) probe_kernel<1><<<blocks, threads, 0, stream>>>(iters, 1.0);
+    else if (which == 7) probe_kernel<2><<<blocks, threads, 0, stream>>>(iters, 1.0);
     else probe_ffma_kernel<<<blocks, threads, 0, stream>>>(iters, 1.0f);
   };
   int iters = 256;
