@@ -393,6 +393,8 @@ def grouped_section(count, steps=5, seed=1907, dtype="fp64"):
     probs = qsynth.grouped_problems(count, seed)
     batch = []
     flops = 0.0
+    nbytes = 0.0   # algorithmic: read A, B, C and write C once
+    esize = 4.0 if dtype == "split_bf16" else 8.0
     for p in probs:
         ra, ca = qsynth.stored_shape(p["opA"], p["m"], p["k"])
         rb, cb = qsynth.stored_shape(p["opB"], p["k"], p["n"])
@@ -401,6 +403,7 @@ def grouped_section(count, steps=5, seed=1907, dtype="fp64"):
         C = torch.randn((p["n"], p["m"], 4), dtype=tdt, device=dev, generator=gen)
         batch.append(dict(p, A=A, B=B, C=C))
         flops += 32.0 * p["m"] * p["n"] * p["k"]
+        nbytes += 4 * esize * (p["m"] * p["k"] + p["k"] * p["n"] + 2 * p["m"] * p["n"])
     C0 = [b["C"].clone() for b in batch]
     t0 = time.perf_counter()
     gb = GroupedBatch(batch, precision=dtype)
@@ -441,7 +444,9 @@ def grouped_section(count, steps=5, seed=1907, dtype="fp64"):
     return {"config": "grouped %s qgemm: %d problems, m,n,k iid U[8,256], ops iid {N,H}, "
                       "interleaved, persistent launch(es) in a CUDA graph" % (dtype, count),
             "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_launch": ms,
-            "flops_per_launch": flops, "tiles": int(gb.plan.tiles), "grid": int(gb.plan.grid),
+            "flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
+            "achieved_gbs_algorithmic": nbytes / (ms * 1e-3) / 1e9,
+            "tiles": int(gb.plan.tiles), "grid": int(gb.plan.grid),
             "prepare_ms_host": prep_ms, "rel_err_sampled_worst": worst,
             "tolerance": 2e-6 if dtype == "split_bf16" else 1e-12,
             "workspace_bytes": int(gb.ws.numel())}
