@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--sliced-size", type=int, default=0, help="default: --size")
     p.add_argument("--no-grouped", action="store_true")
     p.add_argument("--grouped-count", type=int, default=4096)
+    p.add_argument("--no-linear", action="store_true")
     return p.parse_args()
 
 
@@ -452,6 +453,95 @@ def grouped_section(count, steps=5, seed=1907, dtype="fp64"):
             "workspace_bytes": int(gb.ws.numel())}
 
 
+# ----------------------------------------------------- linear section ---
+def linear_section(mb=8192, k=1024, n=1024, steps=5):
+    """One training step of the quaternion linear layer Y = X W through
+    torch.autograd (FP32 storage, split-BF16 products): X mb x k with
+    components N(0,1), W k x n with components N(0, 1/(4k)), loss sum |Y|^2.
+    Times the whole step (forward, loss, backward) and each of its three
+    products alone; reports 3 * 32 mb k n / t and sampled errors of Y, dX and
+    dW (for a seeded dY) against the FP64 oracle."""
+    import numpy as np
+    import torch
+
+    import qsynth
+    from paper_1903_05575_gb300 import ops
+    from paper_1903_05575_gb300.autograd import qlinear
+    dev = torch.device("cuda", torch.cuda.current_device())
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2401)
+    X = torch.randn((k, mb, 4), dtype=torch.float32, device=dev, generator=gen)
+    W = torch.randn((n, k, 4), dtype=torch.float32, device=dev, generator=gen)
+    W.mul_((1.0 / (4.0 * k)) ** 0.5)
+    W.requires_grad_(True)
+    Xg = X.clone().requires_grad_(True)
+    dY = torch.randn((n, mb, 4), dtype=torch.float32, device=dev, generator=gen)
+    Y = torch.empty_like(dY)
+    dX, dW = torch.empty_like(X), torch.empty_like(W.detach())
+    one, zero = (1.0, 0.0, 0.0, 0.0), (0.0, 0.0, 0.0, 0.0)
+    Wd = W.detach()
+    ws = ops.workspace(max(ops._abi.lib().qgemm_backward_workspace_bytes(mb, k, n, 0, 1),
+                           ops._abi.lib().qgemm_workspace_bytes(0, 0, mb, n, k, 0, 1)), dev)
+
+    def train_step():
+        Xg.grad = None
+        W.grad = None
+        out = qlinear(Xg, W)
+        loss = out.square().sum()
+        loss.backward()
+
+    parts = {
+        "step": train_step,
+        "forward": lambda: ops.qgemm("N", "N", mb, n, k, one, X, Wd, zero, Y, ws=ws),
+        "backward_dX": lambda: ops.qgemm_backward(X, Wd, dY, mb, k, n, dX=dX, ws=ws),
+        "backward_dW": lambda: ops.qgemm_backward(X, Wd, dY, mb, k, n, dW=dW, ws=ws),
+    }
+    cur = torch.cuda.current_stream()
+    times = {}
+    for name, fn in parts.items():
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        for _ in range(steps):
+            fn()
+        e1.record(cur)
+        torch.cuda.synchronize()
+        times[name] = e0.elapsed_time(e1) / steps
+    gemm_flops = 32.0 * mb * k * n
+    # sampled errors of the three products on the explicit inputs
+    for fn in ("forward", "backward_dX", "backward_dW"):
+        parts[fn]()
+    torch.cuda.synchronize()
+    from oracle import oracle as orc
+    Xh, Wh, dYh = (T.detach().double().cpu().numpy() for T in (X, Wd, dY))
+    g = np.random.default_rng(12)
+    errs = {}
+    for name, got, opA, opB, M, N, K, A, B in (
+            ("Y", Y, "N", "N", mb, n, k, Xh, Wh),
+            ("dX", dX, "N", "H", mb, k, n, dYh, Wh),
+            ("dW", dW, "H", "N", k, n, mb, Xh, dYh)):
+        rows, cols = g.integers(0, M, 256), g.integers(0, N, 256)
+        ref = orc.qgemm_entries(opA, opB, M, N, K, one, A, B, zero, qsynth.empty(M, N),
+                                rows, cols)
+        G = qsynth.components(got.double().cpu().numpy(), M, "interleaved")[rows, cols]
+        errs[name] = float(np.linalg.norm(G - ref) / np.linalg.norm(ref))
+    return {"config": "quaternion linear layer Y = X W, X %d x %d, W %d x %d quaternions, "
+                      "fp32 storage, split-bf16 products, loss sum |Y|^2, torch.autograd"
+                      % (mb, k, k, n),
+            "value": 3.0 * gemm_flops / (times["step"] * 1e-3) / 1e12, "unit": "TFLOP/s",
+            "ms_per_step": times["step"],
+            "ms_forward": times["forward"], "ms_backward_dX": times["backward_dX"],
+            "ms_backward_dW": times["backward_dW"],
+            "tflops_forward": gemm_flops / (times["forward"] * 1e-3) / 1e12,
+            "tflops_backward_dX": gemm_flops / (times["backward_dX"] * 1e-3) / 1e12,
+            "tflops_backward_dW": gemm_flops / (times["backward_dW"] * 1e-3) / 1e12,
+            "rel_err_sampled": errs, "tolerance": 2e-6,
+            "our_kernels_per_step": 9,
+            "note": "the step also runs torch's square, sum and their backward"}
+
+
 # -------------------------------------------------------------- impls ---
 def run_reference(args):
     """The oracle as the reference arm: each step is a bounded sample of the
@@ -660,6 +750,10 @@ def run_ours(args):
     if not args.no_sliced:
         sliced = sliced_section(args.sliced_size or n, achieved)
 
+    linear = None
+    if not args.no_linear:
+        linear = linear_section()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_baseline(n, layout=layout)
@@ -687,6 +781,7 @@ def run_ours(args):
         "grouped_fp64": grouped,
         "grouped_split_bf16": grouped_split,
         "grouped_fp64_sliced_bf16": grouped_sliced,
+        "linear_layer_split_bf16": linear,
     }
     print(json.dumps(line), flush=True)
 
