@@ -386,79 +386,109 @@ __device__ __forceinline__ void tile_of(int t, const GemmParams &single, const C
   }
 }
 
+// Address of element (ci, cj) of C: the first component (interleaved) or the
+// component-0 plane entry (planes).
+__device__ __forceinline__ float *c_elem(const GemmParams &g, int64_t ci, int64_t cj) {
+  return g.layout == QGEMM_INTERLEAVED ? g.C + 4 * (ci + cj * g.ldc) : g.C + ci + cj * g.ldc;
+}
+
+// Prefetches into L2 the C elements that epilogue() will read for row i and
+// the 32 quaternion columns from nbase (only those inside C).  Issued when a
+// tile's first chunk reaches the drain, so the epilogue's reads of C hit L2
+// instead of waiting on DRAM one element after another.
+__device__ __forceinline__ void prefetch_c(const GemmParams &g, int64_t i, int64_t nbase) {
+  if (g.beta_zero || i >= g.m) return;
+#pragma unroll 4
+  for (int q = 0; q < 32; ++q) {
+    const int64_t nn = nbase + q;
+    if (nn >= g.n) break;
+    const int64_t ci = g.swap ? nn : i, cj = g.swap ? i : nn;
+    const float *e = c_elem(g, ci, cj);
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(e));
+    if (g.layout != QGEMM_INTERLEAVED) {
+#pragma unroll
+      for (int s = 1; s < 4; ++s) asm volatile("prefetch.global.L2 [%0];" ::"l"(e + s * g.psC));
+    }
+  }
+}
+
 // Epilogue of one tile for one drain thread: row i, 32 quaternion columns
 // starting at nbase, accumulated P in acc.  out = alpha P + beta C (left
 // products); alpha P and beta C in FP32, their sum in FP64, one rounding.
+// C is read in batches of kCBatch elements, all loads of a batch before its
+// stores (a larger batch does not fit the drain warps' register budget).
+constexpr int kCBatch = 4;
 __device__ __forceinline__ void epilogue(const GemmParams &g, int64_t i, int64_t nbase,
                                          const float (&acc)[128]) {
   if (i >= g.m) return;
   if (g.tri == 2 && nbase + 31 < i) return;
-  float sa[4][4], sb[4][4];
+  float al[4], be[4];
 #pragma unroll
-  for (int c = 0; c < 4; ++c)
+  for (int s = 0; s < 4; ++s) {
+    al[s] = g.alpha[s];
+    be[s] = g.beta[s];
+  }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int s = c ^ j;
-      sa[c][j] = basis_sign(s, j) < 0 ? -g.alpha[s] : g.alpha[s];
-      sb[c][j] = basis_sign(s, j) < 0 ? -g.beta[s] : g.beta[s];
+  for (int qb = 0; qb < 32; qb += kCBatch) {
+    float cin[kCBatch][4];
+#pragma unroll
+    for (int u = 0; u < kCBatch; ++u) {
+      const int64_t nn = nbase + qb + u;
+#pragma unroll
+      for (int s = 0; s < 4; ++s) cin[u][s] = 0.f;
+      if (g.beta_zero || nn >= g.n) continue;
+      // element (ci, cj) of C; a transposed problem holds (AB)^H: take conj(D)^T
+      const int64_t ci = g.swap ? nn : i, cj = g.swap ? i : nn;
+      const float *src = c_elem(g, ci, cj);
+      if (g.layout == QGEMM_INTERLEAVED && g.c_vec4) {
+        const float4 c4 = *reinterpret_cast<const float4 *>(src);
+        cin[u][0] = c4.x; cin[u][1] = c4.y; cin[u][2] = c4.z; cin[u][3] = c4.w;
+      } else {
+        const int64_t step = g.layout == QGEMM_INTERLEAVED ? 1 : g.psC;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) cin[u][s] = src[s * step];
+      }
     }
 #pragma unroll
-  for (int q = 0; q < 32; ++q) {
-    const int64_t nn = nbase + q;
-    if (nn >= g.n) continue;
-    if ((g.tri == 1 && i < nn) || (g.tri == 2 && i > nn)) continue;
-    float P[4] = {acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]};
-    // element (ci, cj) of C; a transposed problem holds (AB)^H: take conj(D)^T
-    int64_t ci = i, cj = nn;
-    if (g.swap) {
-      ci = nn;
-      cj = i;
-      P[1] = -P[1];
-      P[2] = -P[2];
-      P[3] = -P[3];
-    }
-    float cin[4] = {0.f, 0.f, 0.f, 0.f};
-    float *dst0;
-    if (g.layout == QGEMM_INTERLEAVED) {
-      dst0 = g.C + 4 * (ci + cj * g.ldc);
-      if (!g.beta_zero) {
-        if (g.c_vec4) {
-          const float4 c4 = *reinterpret_cast<const float4 *>(dst0);
-          cin[0] = c4.x; cin[1] = c4.y; cin[2] = c4.z; cin[3] = c4.w;
-        } else {
+    for (int u = 0; u < kCBatch; ++u) {
+      const int q = qb + u;
+      const int64_t nn = nbase + q;
+      if (nn >= g.n) continue;
+      if ((g.tri == 1 && i < nn) || (g.tri == 2 && i > nn)) continue;
+      float P[4] = {acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]};
+      const int64_t ci = g.swap ? nn : i, cj = g.swap ? i : nn;
+      if (g.swap) {
+        P[1] = -P[1];
+        P[2] = -P[2];
+        P[3] = -P[3];
+      }
+      float out[4];
 #pragma unroll
-          for (int s = 0; s < 4; ++s) cin[s] = dst0[s];
+      for (int c = 0; c < 4; ++c) {
+        float ap = 0.f, bc = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int s = c ^ j;  // the sign is a compile-time constant here
+          const bool neg = basis_sign(s, j) < 0;
+          ap = fmaf(neg ? -al[s] : al[s], P[j], ap);
+          bc = fmaf(neg ? -be[s] : be[s], cin[u][j], bc);
         }
+        out[c] = g.beta_zero
+                     ? ap
+                     : static_cast<float>(static_cast<double>(ap) + static_cast<double>(bc));
       }
-    } else {
-      dst0 = g.C + ci + cj * g.ldc;
-      if (!g.beta_zero) {
+      if (g.tri && i == nn) out[1] = out[2] = out[3] = 0.f;  // Hermitian diagonal is real
+      float *dst0 = c_elem(g, ci, cj);
+      if (g.layout == QGEMM_INTERLEAVED) {
+        if (g.c_vec4)
+          *reinterpret_cast<float4 *>(dst0) = make_float4(out[0], out[1], out[2], out[3]);
+        else
 #pragma unroll
-        for (int s = 0; s < 4; ++s) cin[s] = dst0[s * g.psC];
+          for (int s = 0; s < 4; ++s) dst0[s] = out[s];
+      } else {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) dst0[s * g.psC] = out[s];
       }
-    }
-    float out[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      float ap = 0.f, bc = 0.f;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        ap = fmaf(sa[c][j], P[j], ap);
-        bc = fmaf(sb[c][j], cin[j], bc);
-      }
-      out[c] = g.beta_zero ? ap
-                           : static_cast<float>(static_cast<double>(ap) + static_cast<double>(bc));
-    }
-    if (g.tri && i == nn) out[1] = out[2] = out[3] = 0.f;  // Hermitian diagonal is real
-    if (g.layout == QGEMM_INTERLEAVED) {
-      if (g.c_vec4)
-        *reinterpret_cast<float4 *>(dst0) = make_float4(out[0], out[1], out[2], out[3]);
-      else
-#pragma unroll
-        for (int s = 0; s < 4; ++s) dst0[s] = out[s];
-    } else {
-#pragma unroll
-      for (int s = 0; s < 4; ++s) dst0[s * g.psC] = out[s];
     }
   }
 }
@@ -605,6 +635,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       int kb_lo, kb_hi;
       kb_range(*g, mt, nt, kb_lo, kb_hi);
       const int nch = (kb_hi - kb_lo + chunk - 1) / chunk;
+      prefetch_c(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane,
+                 static_cast<int64_t>(nt) * BNQ + 32 * half);
       float acc[128];
 #pragma unroll
       for (int i = 0; i < 128; ++i) acc[i] = 0.f;
@@ -1014,6 +1046,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
       if (tile_skip(*g, mt, nt)) continue;
       const int nkb = g->num_kb;
       const int nch = (nkb + chunk - 1) / chunk;
+      prefetch_c(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane,
+                 static_cast<int64_t>(nt) * BNQ + 32 * half);
       float acc[128];
 #pragma unroll
       for (int i = 0; i < 128; ++i) acc[i] = 0.f;
