@@ -1336,7 +1336,9 @@ int prepare_sliced_grouped(const std::vector<GemmDesc> &in, int layout, unsigned
   plan->workspace_bytes = L.total;
   plan->tiles = L.tiles;
   plan->grid = static_cast<int32_t>(std::min<int64_t>(std::max<int64_t>(L.tiles, 1), sms));
-  plan->reserved0 = 8 * sms;  // pre-pass CTAs (grid-stride over the tile lists)
+  // pre-pass CTAs (grid-stride over the tile lists): many small tiles, so up
+  // to 64 CTAs per SM keep more of them in flight than 8 do
+  plan->reserved0 = 64 * sms;
   plan->desc_offset = static_cast<int64_t>(L.desc_off);
   plan->tile_offset = static_cast<int64_t>(L.tile_off);
   plan->data_offset = static_cast<int64_t>(L.max_off);

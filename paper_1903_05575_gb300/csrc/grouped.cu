@@ -154,8 +154,9 @@ struct GroupedErr {
 };
 
 // Pre-pass over the split operands of every problem: entry = (problem,
-// is_b, row tile, k tile).
-__global__ void __launch_bounds__(256)
+// is_b, row tile, k tile).  At most 32 registers, so 8 CTAs fit on an SM: the
+// tiles are small and ragged, and more resident CTAs keep more loads in flight.
+__global__ void __launch_bounds__(256, 8)
     grouped_prepass_kernel(const split::SplitProb *__restrict__ probs,
                            const int4 *__restrict__ ptiles, int n) {
   __shared__ float4 tile[32][33];
@@ -437,8 +438,9 @@ int prepare_split(const std::vector<GemmDesc> &ds_in, int layout, unsigned char 
   plan->workspace_bytes = L.total;
   plan->tiles = L.tiles;
   plan->grid = static_cast<int32_t>(std::min<int64_t>(std::max<int64_t>(L.tiles, 1), sms));
+  // pre-pass CTAs: up to 64 per SM (grid-stride beyond), 8 resident per SM
   plan->reserved0 = static_cast<int32_t>(
-      std::min<int64_t>(std::max<int64_t>(L.ptiles, 1), static_cast<int64_t>(sms) * 8));
+      std::min<int64_t>(std::max<int64_t>(L.ptiles, 1), static_cast<int64_t>(sms) * 64));
   plan->desc_offset = static_cast<int64_t>(L.desc_off);
   plan->tile_offset = static_cast<int64_t>(L.tile_off);
   plan->data_offset = static_cast<int64_t>(L.data_off);
