@@ -898,35 +898,41 @@ __device__ __forceinline__ void slice_tile(const SliceArgs &p, int64_t rt, int64
     const double4 v = tile[kk][rr];
     const int sft = sm.shift[rr];
     const double comp[4] = {v.x, v.y, v.z, v.w};
-    int d[4][NSL];
+    long long X[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j)  // a non-finite row gets digits 0 (its C entries NaN)
-      digits6(sft == kNonFinite ? 0ll : round_scaled(comp[j], sft), d[j]);
-    // BF16 bits of each digit (exact: |d| <= 256); a sign flip is an XOR
-    uint32_t hb[4][NSL];
+      X[j] = sft == kNonFinite ? 0ll : round_scaled(comp[j], sft);
+    // Balanced base-256 digits as in digits6, least significant (t = 5) first,
+    // so only the four remainders stay live; each digit's BF16 bits are exact
+    // (|d| <= 256) and a sign flip is an XOR.
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int t = NSL - 1; t >= 0; --t) {
+      uint32_t hb[4];
 #pragma unroll
-      for (int t = 0; t < NSL; ++t) hb[j][t] = __float_as_uint(static_cast<float>(d[j][t])) >> 16;
-    if (!IS_B) {
-#pragma unroll
-      for (int t = 0; t < NSL; ++t)
-        store_bits(p.out + t * p.slice_stride + r * p.kp + p.kw * kq, hb[0][t] | (hb[1][t] << 16),
-                   hb[2][t] | (hb[3][t] << 16), p.kw);
-    } else {
-#pragma unroll
-      for (int t = 0; t < NSL; ++t)
+      for (int j = 0; j < 4; ++j) {
+        long long dj = X[j];
+        if (t > 0) {
+          dj = ((X[j] + 128) & 255) - 128;
+          X[j] = (X[j] - dj) >> 8;
+        }
+        hb[j] = __float_as_uint(static_cast<float>(static_cast<int>(dj))) >> 16;
+      }
+      if (!IS_B) {
+        store_bits(p.out + t * p.slice_stride + r * p.kp + p.kw * kq, hb[0] | (hb[1] << 16),
+                   hb[2] | (hb[3] << 16), p.kw);
+      } else {
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          uint32_t v[4];
+          uint32_t w[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const int q = j ^ c;
-            v[j] = hb[q][t] ^ (basis_sign(j, q) < 0 ? 0x8000u : 0u);
+            w[j] = hb[q] ^ (basis_sign(j, q) < 0 ? 0x8000u : 0u);
           }
           store_bits(p.out + t * p.slice_stride + (4 * r + c) * p.kp + p.kw * kq,
-                     v[0] | (v[1] << 16), v[2] | (v[3] << 16), p.kw);
+                     w[0] | (w[1] << 16), w[2] | (w[3] << 16), p.kw);
         }
+      }
     }
   }
 }
@@ -937,18 +943,20 @@ __global__ void __launch_bounds__(256) slice_kernel(const SliceArgs p) {
   slice_tile<IS_B>(p, blockIdx.x, blockIdx.y, sm);
 }
 
-// Grouped: stiles[t] = (problem, operand 0 A / 1 B, row tile, k tile).
-__global__ void __launch_bounds__(256)
+// Grouped: stiles[0].x = the number of A tiles nA, then nA entries (problem,
+// 0, row tile, k tile) of A operands and the B entries (problem, 1, ...).
+// One launch per operand kind, so each compiles to the registers of its own
+// path rather than the maximum of both (A: 40, six CTAs per SM; B: 48, five).
+template <bool IS_B>
+__global__ void __launch_bounds__(256, IS_B ? 5 : 6)
     grouped_slice_kernel(const SlicedProb *__restrict__ probs, const int4 *__restrict__ stiles,
                          int n) {
   __shared__ SliceSmem sm;
-  for (int t = blockIdx.x; t < n; t += gridDim.x) {
+  const int na = stiles[0].x;
+  const int lo = IS_B ? 1 + na : 1, hi = IS_B ? n : 1 + na;
+  for (int t = lo + static_cast<int>(blockIdx.x); t < hi; t += gridDim.x) {
     const int4 e = stiles[t];
-    const SlicedProb &pr = probs[e.x];
-    if (e.y)
-      slice_tile<true>(pr.sb, e.z, e.w, sm);
-    else
-      slice_tile<false>(pr.sa, e.z, e.w, sm);
+    slice_tile<IS_B>(IS_B ? probs[e.x].sb : probs[e.x].sa, e.z, e.w, sm);
     __syncthreads();
   }
 }
@@ -1207,6 +1215,7 @@ GroupedLayout grouped_layout(const std::vector<GemmDesc> &in) {
   L.a_off.assign(P, 0);
   L.b_off.assign(P, 0);
   L.kp.assign(P, 0);
+  L.stiles = 1;  // the slicing list's header entry (number of A tiles)
   size_t maxb_total = 0, exp_total = 0, data = 0;
   for (size_t p = 0; p < P; ++p) {
     bool sw = false;
@@ -1269,8 +1278,9 @@ int prepare_sliced_grouped(const std::vector<GemmDesc> &in, int layout, unsigned
   if (rc) return rc;
   std::vector<unsigned char> host(L.max_off - L.desc_off, 0);
   auto *hd = reinterpret_cast<SlicedProb *>(host.data());
-  std::vector<int4> tiles, mtiles, stiles;
+  std::vector<int4> tiles, mtiles, stiles, stiles_b;
   std::vector<int> tile_kb;
+  stiles.push_back(make_int4(0, 0, 0, 0));  // header: the number of A tiles
   for (size_t p = 0; p < L.ds.size(); ++p) {
     const GemmDesc &d = L.ds[p];
     if (d.m == 0 || d.n == 0) continue;
@@ -1307,8 +1317,8 @@ int prepare_sliced_grouped(const std::vector<GemmDesc> &in, int layout, unsigned
                                      static_cast<int>(c)));
       for (int64_t r = 0; r < (d.n + 31) / 32; ++r)
         for (int64_t c = 0; c < kt; ++c)
-          stiles.push_back(make_int4(static_cast<int>(p), 1, static_cast<int>(r),
-                                     static_cast<int>(c)));
+          stiles_b.push_back(make_int4(static_cast<int>(p), 1, static_cast<int>(r),
+                                       static_cast<int>(c)));
     }
     for (int a = 0; a < q.g.num_mt; ++a)
       for (int b = 0; b < q.g.num_nt; ++b) {
@@ -1325,6 +1335,9 @@ int prepare_sliced_grouped(const std::vector<GemmDesc> &in, int layout, unsigned
   for (size_t i = 0; i < order.size(); ++i) ht[i] = tiles[order[i]];
   std::memcpy(host.data() + (L.mtile_off - L.desc_off), mtiles.data(),
               mtiles.size() * sizeof(int4));
+  stiles[0].x = static_cast<int>(stiles.size() - 1);
+  stiles.insert(stiles.end(), stiles_b.begin(), stiles_b.end());
+  if (static_cast<int64_t>(stiles.size()) != L.stiles) return QGEMM_ERR_UNSUPPORTED;
   std::memcpy(host.data() + (L.stile_off - L.desc_off), stiles.data(),
               stiles.size() * sizeof(int4));
   if (!host.empty() && cudaMemcpyAsync(ws + L.desc_off, host.data(), host.size(),
@@ -1365,7 +1378,10 @@ int launch_sliced_grouped(const qgemm_grouped_plan *plan, cudaStream_t s) {
     return launch_status();
   const int pgrid = plan->reserved0 > 0 ? plan->reserved0 : 1;
   if (nm > 0) grouped_slice_max_kernel<<<std::min(nm, pgrid), 256, 0, s>>>(probs, mtiles, nm);
-  if (ns > 0) grouped_slice_kernel<<<std::min(ns, pgrid), 256, 0, s>>>(probs, stiles, ns);
+  if (ns > 1) {  // entry 0 is the header
+    grouped_slice_kernel<false><<<std::min(ns - 1, pgrid), 256, 0, s>>>(probs, stiles, ns);
+    grouped_slice_kernel<true><<<std::min(ns - 1, pgrid), 256, 0, s>>>(probs, stiles, ns);
+  }
   CUtensorMap none;
   std::memset(&none, 0, sizeof(none));
   const SlicedParams unused{};
