@@ -27,7 +27,15 @@
  *
  * Precision:
  *   QGEMM_FP64:            double data; products on FP64 tensor cores (DMMA),
- *                          FP64 accumulation and epilogue.
+ *                          FP64 accumulation and epilogue.  Needs no
+ *                          workspace; given one of qgemm_workspace_bytes()
+ *                          bytes, a product whose C is too small to fill the
+ *                          GPU (fewer than 8 waves of 16 x 16 quaternion
+ *                          tiles, the last one part-empty) and whose k is long
+ *                          splits K across CTAs so that the waves fill:
+ *                          each share's partial product goes to the workspace
+ *                          and a second kernel sums the shares in a fixed
+ *                          order (deterministic) before the epilogue.
  *   QGEMM_FP32_SPLIT_BF16: float data; each operand is split into three BF16
  *                          terms (hi, mid, lo), the six leading term products
  *                          run on the BF16 tensor cores (tcgen05) with FP32
@@ -134,7 +142,8 @@ extern "C" {
  *  18 precision          QGEMM_FP64, QGEMM_FP32_SPLIT_BF16 or
  *                        QGEMM_FP64_SLICED_BF16
  *  19 workspace          device scratch, 256-byte aligned, or NULL if
- *  20 workspace_bytes    qgemm_workspace_bytes() is 0
+ *  20 workspace_bytes    qgemm_workspace_bytes() is 0 (optional for
+ *                        QGEMM_FP64: NULL or a smaller one runs K unsplit)
  *  21 stream             cudaStream_t
  */
 int qgemm(int opA, int opB, int64_t m, int64_t n, int64_t k,
@@ -147,8 +156,10 @@ int qgemm(int opA, int opB, int64_t m, int64_t n, int64_t k,
           void *workspace, size_t workspace_bytes,
           void *stream);
 
-/* Workspace qgemm() needs for these arguments (0 for QGEMM_FP64).  Returns 0
- * for invalid arguments as well; qgemm() itself reports those. */
+/* Workspace qgemm() needs for these arguments; for QGEMM_FP64 the workspace
+ * that lets it split K (0 when the product would not be split; the SM count
+ * of the current device decides, 152 when there is none).  Returns 0 for
+ * invalid arguments as well; qgemm() itself reports those. */
 size_t qgemm_workspace_bytes(int opA, int opB, int64_t m, int64_t n, int64_t k,
                              int layout, int precision);
 

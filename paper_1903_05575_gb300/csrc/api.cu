@@ -145,7 +145,7 @@ int workspace_need(const GemmDesc &d, int precision, size_t *need) {
 
 int launch_product(const GemmDesc &d, int precision, void *ws, size_t ws_bytes,
                    cudaStream_t s) {
-  if (precision == QGEMM_FP64) return launch_fp64_gemm(d, s);
+  if (precision == QGEMM_FP64) return launch_fp64_gemm_ws(d, ws, ws_bytes, s);
   if (precision == QGEMM_FP64_SLICED_BF16) return launch_sliced_gemm(d, ws, ws_bytes, s);
   return launch_split_gemm(d, ws, ws_bytes, s);
 }
@@ -206,7 +206,7 @@ int qgemm_split_noalloc(int opA, int opB, int64_t m, int64_t n, int64_t k,
 
 size_t qgemm_workspace_bytes(int opA, int opB, int64_t m, int64_t n, int64_t k, int layout,
                              int precision) {
-  if (precision != QGEMM_FP32_SPLIT_BF16 && precision != QGEMM_FP64_SLICED_BF16) return 0;
+  if (!precision_ok(precision)) return 0;
   if (opA < 0 || opA > 3 || opB < 0 || opB > 3 || m < 0 || n < 0 || k < 0) return 0;
   if (layout != QGEMM_INTERLEAVED && layout != QGEMM_SPLIT_PLANES) return 0;
   if (m == 0 || n == 0 || k == 0) return 0;
@@ -217,6 +217,8 @@ size_t qgemm_workspace_bytes(int opA, int opB, int64_t m, int64_t n, int64_t k, 
   d.n = n;
   d.k = k;
   d.layout = layout;
+  // FP64: optional; this much lets a small-m n, long-k product split K
+  if (precision == QGEMM_FP64) return fp64_splitk_bytes(m, n, fp64_ksplit(d, device_sms()));
   size_t b = 0;
   if (workspace_need(d, precision, &b)) return 0;
   return b;
@@ -263,6 +265,7 @@ size_t qherk_workspace_bytes(int uplo, int trans, int64_t n, int64_t k, int layo
                              int precision) {
   (void)uplo;
   if (trans != QGEMM_OP_N && trans != QGEMM_OP_H) return 0;
+  if (precision == QGEMM_FP64) return 0;  // a triangle is never split along K
   return qgemm_workspace_bytes(trans, trans == QGEMM_OP_N ? QGEMM_OP_H : QGEMM_OP_N, n, n, k,
                                layout, precision);
 }

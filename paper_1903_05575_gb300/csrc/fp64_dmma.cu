@@ -66,6 +66,52 @@ __global__ void __launch_bounds__(kThreads)
                                        p.limit_ns, &g_fp64_error);
 }
 
+// K split: P = sum over z of the partial products (z ascending, so the result
+// does not depend on the order the CTAs finished), then C <- alpha P + beta C
+// with left products in FP64; beta == 0 does not read C.
+template <int LAYOUT>
+__global__ void __launch_bounds__(256)
+    splitk_reduce_kernel(const double *__restrict__ part, int ksplit, int64_t m, int64_t n,
+                         double *C, int64_t ldc, int64_t psC, double a0, double a1, double a2,
+                         double a3, double b0, double b1, double b2, double b3, int beta_zero) {
+  const double al[4] = {a0, a1, a2, a3}, be[4] = {b0, b1, b2, b3};
+  const int64_t total = m * n, slab = total * 4;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    double P[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int z = 0; z < ksplit; ++z) {
+      const double2 *q = reinterpret_cast<const double2 *>(part + z * slab + 4 * e);
+      const double2 lo = q[0], hi = q[1];
+      P[0] += lo.x;
+      P[1] += lo.y;
+      P[2] += hi.x;
+      P[3] += hi.y;
+    }
+    const int64_t i = e % m, j = e / m;
+    double *q[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+      q[s] = LAYOUT == QGEMM_INTERLEAVED ? C + 4 * (i + j * ldc) + s : C + s * psC + i + j * ldc;
+    double c[4] = {0.0, 0.0, 0.0, 0.0};
+    if (!beta_zero) {
+#pragma unroll
+      for (int s = 0; s < 4; ++s) c[s] = *q[s];
+    }
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      double v = 0.0;
+#pragma unroll
+      for (int j2 = 0; j2 < 4; ++j2) {
+        const int s = cc ^ j2;
+        const double sg = basis_sign(s, j2) < 0 ? -1.0 : 1.0;
+        v = fma(sg * al[s], P[j2], v);
+        if (!beta_zero) v = fma(sg * be[s], c[j2], v);
+      }
+      *q[cc] = v;
+    }
+  }
+}
+
 // C <- beta C (k == 0 or alpha == 0), or C <- 0 when beta == 0.
 template <typename T, int LAYOUT>
 __global__ void scale_kernel(T *C, int64_t m, int64_t n, int64_t ldc, int64_t psC, double b0,
@@ -205,10 +251,73 @@ fp64::Operands fp64_operands(const GemmDesc &d) {
   return a;
 }
 
+int launch_keyed(int key, const CUtensorMap &tmA, const CUtensorMap &tmB, const Fp64Args &a,
+                 dim3 grid, cudaStream_t stream);
+
+// Number of K shares for the single-problem FP64 kernel.  With 16 x 16
+// quaternion tiles and 2 CTAs per SM, a launch of w = tiles * s / (2 SMs)
+// waves keeps the FP64 pipes busy for a fraction w / ceil(w) of its time.  For
+// C of fewer than 8 waves of tiles, take the fewest shares s in [2, 256]
+// whose fraction is within 2 % of the best, keeping at least 8 k-blocks (128
+// quaternion k) per share, and split only when the best gains 5 % over s = 1.
+// Plain products only (no triangle, k-range or turned-around problem).
+int fp64_ksplit(const GemmDesc &d, int sms) {
+  if (d.tri || d.krange || d.swap || d.kwidth != 4 || d.m <= 0 || d.n <= 0) return 1;
+  const int64_t tiles = ((d.m + 15) / 16) * ((d.n + 15) / 16);
+  const int64_t slots = 2LL * sms;
+  if (tiles >= 8 * slots) return 1;
+  const int64_t ktiles = (d.k + kBKQ - 1) / kBKQ;
+  const int64_t smax = std::min<int64_t>(256, ktiles / 8);
+  auto busy = [&](int64_t s) {
+    const int64_t ctas = tiles * s;
+    const int64_t waves = (ctas + slots - 1) / slots;
+    return static_cast<double>(ctas) / static_cast<double>(waves * slots);
+  };
+  double top = busy(1);
+  for (int64_t s = 2; s <= smax; ++s) top = std::max(top, busy(s));
+  if (top < busy(1) + 0.05) return 1;
+  for (int64_t s = 2; s <= smax; ++s)  // fewest shares within 2 % of the best
+    if (busy(s) >= top - 0.02) return static_cast<int>(s);
+  return 1;
+}
+
+size_t fp64_splitk_bytes(int64_t m, int64_t n, int ksplit) {
+  return ksplit > 1 ? static_cast<size_t>(ksplit) * m * n * 4 * sizeof(double) : 0;
+}
+
+int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms <= 0) {
+    cudaGetLastError();
+    return 152;  // GB300
+  }
+  return sms;
+}
+
 int launch_fp64_gemm(const GemmDesc &d, cudaStream_t stream) {
+  return launch_fp64_gemm_ws(d, nullptr, 0, stream);
+}
+
+int launch_fp64_gemm_ws(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_t stream) {
   Fp64Args a{};
   a.op = fp64_operands(d);
   a.limit_ns = wait_limit_ns();
+  // K split when it pays and the caller's workspace holds the partials
+  int ks = fp64_ksplit(d, device_sms());
+  if (ks > 1) {
+    const size_t per = static_cast<size_t>(d.m) * d.n * 4 * sizeof(double);  // one share
+    const int64_t fit = (ws != nullptr && reinterpret_cast<uintptr_t>(ws) % 256 == 0)
+                            ? static_cast<int64_t>(ws_bytes / per)
+                            : 0;
+    if (fit < ks) ks = static_cast<int>(fit);
+    if (ks < 2) ks = 1;
+  }
+  if (ks > 1) {
+    a.op.ksplit = ks;
+    a.op.part = static_cast<double *>(ws);
+  }
   const bool ta = op_trans(d.opA), tb = op_trans(d.opB);
   // 32 x 32 quaternion tiles, or 16 x 16 when 32 x 32 would give fewer than
   // about 32 waves of the 2 CTAs per SM that fit (the last, partial wave
@@ -226,8 +335,27 @@ int launch_fp64_gemm(const GemmDesc &d, cudaStream_t stream) {
   a.op.tmaB = encode_fp64_operand(&tmB, d.B, d.layout, tb ? bn : kBKQ, tb ? kBKQ : bn) ? 1 : 0;
   const int64_t gx = (d.m + bm - 1) / bm, gy = (d.n + bn - 1) / bn;
   if (gx > 0x7fffffff || gy > 65535) return QGEMM_ERR_UNSUPPORTED;
-  dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy));
+  dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy), static_cast<unsigned>(ks));
   const int key = (small ? 8 : 0) | (d.layout << 2) | (ta << 1) | tb;
+  const int rc = launch_keyed(key, tmA, tmB, a, grid, stream);
+  if (rc || ks == 1) return rc;
+  const int64_t total = d.m * d.n;
+  const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152LL * 16);
+  double *C = static_cast<double *>(d.C);
+  const double *al = d.alpha, *be = d.beta;
+  if (d.layout == QGEMM_INTERLEAVED)
+    splitk_reduce_kernel<QGEMM_INTERLEAVED><<<static_cast<unsigned>(blocks), 256, 0, stream>>>(
+        a.op.part, ks, d.m, d.n, C, d.ldc, d.psc, al[0], al[1], al[2], al[3], be[0], be[1],
+        be[2], be[3], d.beta_zero ? 1 : 0);
+  else
+    splitk_reduce_kernel<QGEMM_SPLIT_PLANES><<<static_cast<unsigned>(blocks), 256, 0, stream>>>(
+        a.op.part, ks, d.m, d.n, C, d.ldc, d.psc, al[0], al[1], al[2], al[3], be[0], be[1],
+        be[2], be[3], d.beta_zero ? 1 : 0);
+  return launch_status();
+}
+
+int launch_keyed(int key, const CUtensorMap &tmA, const CUtensorMap &tmB, const Fp64Args &a,
+                 dim3 grid, cudaStream_t stream) {
   switch (key) {
     case 0: return launch_typed<0, false, false>(tmA, tmB, a, grid, stream);
     case 1: return launch_typed<0, false, true>(tmA, tmB, a, grid, stream);

@@ -44,6 +44,12 @@ struct Operands {
   int tri;  // 0 full; 1 lower (row >= col) only; 2 upper; diagonal written real
   int krange;  // k-range of a tile when op(A) or op(B) is triangular (see GemmDesc)
   int swap;    // 1: the tile holds D = (op(A) op(B))^H; store C = conj(D)^T
+  // K split across blockIdx.z (single-problem kernel only): CTA z sums its
+  // share of the k-blocks and stores that partial product, four doubles per
+  // quaternion, to part + z m n 4 (dense, interleaved, leading dimension m);
+  // a second kernel sums the ksplit partials and applies alpha and beta.
+  int ksplit;  // 0 or 1: no split
+  double *part;
 };
 
 // True when the tile at quaternion offset (i0, n0) of size BMQ x BNQ has no
@@ -135,6 +141,12 @@ __device__ bool tile(const Operands &p, const CUtensorMap *tmA, const CUtensorMa
   if (p.krange == 2) kt_lo = static_cast<int>(i0 / kBKQ);
   if (p.krange == 3) kt_lo = static_cast<int>(n0 / kBKQ);
   if (p.krange == 4) kt_hi = min(kt_hi, static_cast<int>((n0 + BNQ + kBKQ - 1) / kBKQ));
+  if (p.ksplit > 1) {  // this CTA's share of the k-blocks
+    const int64_t span = kt_hi > kt_lo ? kt_hi - kt_lo : 0, z = blockIdx.z;
+    const int lo = kt_lo + static_cast<int>(span * z / p.ksplit);
+    kt_hi = kt_lo + static_cast<int>(span * (z + 1) / p.ksplit);
+    kt_lo = lo;
+  }
   const int ktiles = kt_hi > kt_lo ? kt_hi - kt_lo : 0;
   const uint32_t tx_bytes = (p.tmaA ? kABytes : 0u) + (p.tmaB ? kBBytes : 0u);
 
@@ -269,6 +281,21 @@ __device__ bool tile(const Operands &p, const CUtensorMap *tmA, const CUtensorMa
     if (tid == 0 && kt + kStages < ktiles) issue(kt + kStages);
   }
   kb_run += ktiles;
+
+  if (p.ksplit > 1) {  // partial product of this K share: each lane its component
+    double *slab = p.part + static_cast<int64_t>(blockIdx.z) * p.m * p.n * 4;
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int cc = 0; cc < NC; ++cc)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int64_t qi = i0 + arow + 4 * r + 2 * (e >> 1);
+          const int64_t qn = n0 + wn * WN + 8 * cc + 2 * t + (e & 1);
+          if (qi < p.m && qn < p.n) slab[4 * (qi + qn * p.m) + c_lane] = acc[r][cc][e];
+        }
+    return true;
+  }
 
   // epilogue: C <- alpha P + beta C, left products, FP64
   double la[4], lb[4];

@@ -71,6 +71,13 @@ inline bool precision_fp64_data(int p) { return p != QGEMM_FP32_SPLIT_BF16; }
 
 // Launchers (return QGEMM status codes).
 int launch_fp64_gemm(const GemmDesc &d, cudaStream_t stream);
+// The FP64 product with an optional caller workspace: when fp64_ksplit() > 1
+// and the workspace holds that many partial products (fp64_splitk_bytes), K
+// is split across CTAs and a second kernel sums the partials.
+int launch_fp64_gemm_ws(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_t stream);
+int fp64_ksplit(const GemmDesc &d, int sms);
+size_t fp64_splitk_bytes(int64_t m, int64_t n, int ksplit);
+int device_sms();  // SM count of the current device (152 when there is none)
 int launch_fp64_mixed(const GemmDesc &d, cudaStream_t stream);
 int launch_scale(const GemmDesc &d, bool fp64, cudaStream_t stream);
 int launch_herk_scale(const GemmDesc &d, bool fp64, cudaStream_t stream);

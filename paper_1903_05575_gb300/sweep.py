@@ -13,6 +13,8 @@ N x N products, Sec. 5), printing one JSON line per case:
          its time relative to the GEMM of the same size.
   mixed: qgemm_mixed with complex / real factors at --mixed sizes on the
          tensor-core precisions.
+  splitk: FP64 products with a small C and a long k (--splitk m x n x k
+         shapes), with and without the workspace that lets K split.
 
 Timing: CUDA events on the launching stream around `reps` calls after
 warm-up; inputs of every case are larger than L2 except the smallest FP64
@@ -219,6 +221,56 @@ def complex_comparison(n, reps, qgemm_ms=None):
             "note": "rates count 32 n^3 flops (the quaternion product) for all three"}
 
 
+def splitk_case(m, n, k, peak, reps):
+    """FP64 product with a small C and a long k, run with the workspace that
+    lets it split K and without one (unsplit); N(0,1) data, op N,N,
+    interleaved, unit-quaternion alpha and beta; error of the split result on
+    sampled entries against the oracle."""
+    import torch
+
+    import qsynth
+    from . import _abi, ops
+    dev = torch.device("cuda", torch.cuda.current_device())
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(m + 3 * n + k)
+    A = torch.randn((k, m, 4), dtype=torch.float64, device=dev, generator=gen)
+    B = torch.randn((n, k, 4), dtype=torch.float64, device=dev, generator=gen)
+    C0 = torch.randn((n, m, 4), dtype=torch.float64, device=dev, generator=gen)
+    C = C0.clone()
+    alpha, beta = qsynth.unit_quaternion(m + 5), qsynth.unit_quaternion(n + 6)
+    L = _abi.lib()
+    need = L.qgemm_workspace_bytes(0, 0, m, n, k, 0, 0)
+    ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def call(w, wb):
+        rc = L.qgemm(0, 0, m, n, k, _abi.q4(alpha), A.data_ptr(), m, 0, B.data_ptr(), k, 0,
+                     _abi.q4(beta), C.data_ptr(), m, 0, 0, 0, w, wb, stream)
+        _abi.check(rc, "qgemm")
+    t_split = _timed(lambda: call(ws.data_ptr(), need), reps)
+    t_plain = _timed(lambda: call(None, 0), reps)
+    C.copy_(C0)
+    call(ws.data_ptr(), need)
+    torch.cuda.synchronize()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    from oracle import oracle as orc
+    g = np.random.default_rng(3)
+    rows, cols = g.integers(0, m, 128), g.integers(0, n, 128)
+    ref = orc.qgemm_entries("N", "N", m, n, k, alpha, A.cpu().numpy(), B.cpu().numpy(), beta,
+                            C0.cpu().numpy(), rows, cols)
+    got = qsynth.components(C.cpu().numpy(), m, "interleaved")[rows, cols]
+    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    flops = 32.0 * m * n * k
+    return {"path": "fp64 split K", "m": m, "n": n, "k": k, "op": "NN", "layout": "interleaved",
+            "workspace_bytes": need, "ms_split": t_split, "ms_unsplit": t_plain,
+            "tflops_split": flops / (t_split * 1e-3) / 1e12,
+            "tflops_unsplit": flops / (t_plain * 1e-3) / 1e12,
+            "frac_of_dmma_peak_split": flops / (t_split * 1e-3) / 1e12 / peak,
+            "speedup": t_plain / t_split, "rel_err_sampled": err, "tolerance": 1e-12}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--sizes", default="1024,2048,4096")
@@ -229,6 +281,8 @@ def main():
     ap.add_argument("--trmm", default="", help="sizes for the triangular product")
     ap.add_argument("--mixed", default="", help="sizes for the mixed-type products")
     ap.add_argument("--mixed-fp64", default="", help="sizes for the FP64 mixed-type products")
+    ap.add_argument("--splitk", default="",
+                    help="m x n x k shapes (e.g. 64x64x65536,256x256x65536) for the FP64 K split")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--compare", default="", help="sizes for the cuBLAS ZGEMM/DGEMM comparison")
     a = ap.parse_args()
@@ -266,6 +320,9 @@ def main():
     for n in [int(x) for x in a.mixed_fp64.split(",") if x]:
         for types in ("HH", "HC", "CH", "HR", "RH"):
             print(json.dumps(mixed_case(n, "fp64", types, 2)), flush=True)
+    for shape in [x for x in a.splitk.split(",") if x]:
+        m, n, k = (int(v) for v in shape.split("x"))
+        print(json.dumps(splitk_case(m, n, k, peak, max(a.reps, 3))), flush=True)
     for n in [int(x) for x in a.compare.split(",") if x]:
         print(json.dumps(complex_comparison(n, a.reps)), flush=True)
 

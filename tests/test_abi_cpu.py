@@ -83,6 +83,42 @@ def test_split_precision_needs_workspace():
                  wsb=need - 1) == -20
 
 
+def test_fp64_split_k_workspace():
+    """FP64 needs no workspace, but reports the one that lets it split K: for
+    C of fewer than 8 waves of 16 x 16 quaternion tiles (2 CTAs per SM, 152
+    SMs without a device), the fewest shares s in [2, min(256, k-blocks / 8)]
+    whose busy fraction (CTAs over whole waves) is within 2 % of the best, if
+    the best gains 5 % over s = 1; s partial products of 32 bytes per
+    quaternion.  0 when
+    nothing is split, and for the Hermitian update (a triangle is never
+    split)."""
+    L = _abi.lib()
+
+    def expect(m, n, k, sms=152):
+        tiles = -(-m // 16) * -(-n // 16)
+        slots = 2 * sms
+        if tiles >= 8 * slots:
+            return 0
+
+        def busy(s):
+            return tiles * s / (-(-tiles * s // slots) * slots)
+        shares = range(2, min(256, (-(-k // 16)) // 8) + 1)
+        top = max([busy(1)] + [busy(s) for s in shares])
+        if top < busy(1) + 0.05:
+            return 0
+        return min(s for s in shares if busy(s) >= top - 0.02) * m * n * 32
+    for (m, n, k) in ((64, 64, 20000), (37, 29, 3000), (300, 300, 4096), (16, 16, 100),
+                      (4096, 4096, 4096), (1, 1, 10000), (400, 390, 50000), (256, 256, 65536),
+                      (128, 128, 131072)):
+        assert L.qgemm_workspace_bytes(0, 0, m, n, k, 0, 0) == expect(m, n, k), (m, n, k)
+    assert L.qgemm_workspace_bytes(0, 0, 64, 64, 20000, 0, 0) > 0
+    assert L.qgemm_workspace_bytes(0, 0, 256, 256, 65536, 0, 0) > 0
+    assert L.qherk_workspace_bytes(0, 0, 64, 20000, 0, 0) == 0
+    # the FP64 call itself never asks for it: no -19 / -20 without a workspace
+    assert _call(m=64, n=64, k=20000, lda=64, ldb=20000, ldc=64, A=64, B=64,
+                 C=64) in (0, _abi.ERR_NO_DEVICE)
+
+
 def test_sliced_precision_workspace():
     """FP64 digit-sliced path: six BF16 slices of A' (m x 4k) and of the
     expanded B' (4n x 4k), K padded to 32 reals, plus per-row and per-column
