@@ -152,3 +152,28 @@ def test_split_runs_faster_than_unsplit():
     t_split, t_plain = timed(ws.data_ptr(), need), timed(None, 0)
     print("split %.2f ms, unsplit %.2f ms" % (t_split, t_plain))
     assert t_split * 3 < t_plain
+
+
+def test_backward_dw_long_batch_splits():
+    """dW = X^H dY of a linear layer with a long batch (mb = 20000) and a
+    small weight (40 x 24): qgemm_backward's workspace lets the FP64 product
+    split its k = mb; dX = dY W^H (20000 x 40) fills the GPU unsplit."""
+    mb, k, n = 20000, 40, 24
+    L = _abi.lib()
+    assert L.qgemm_backward_workspace_bytes(mb, k, n, 0, 0) >= workspace_for("H", "N", k, n, mb,
+                                                                             "interleaved") > 0
+    Xs = qsynth.normal(mb, k, 5600, pad=0.0)
+    Ws = qsynth.normal(k, n, 5601, pad=0.0)
+    dYs = qsynth.normal(mb, n, 5602, pad=0.0)
+    X, W, dY = to_dev(Xs), to_dev(Ws), to_dev(dYs)
+    dX, dW = torch.empty_like(X), torch.empty_like(W)
+    ops.qgemm_backward(X, W, dY, mb, k, n, dX=dX, dW=dW)
+    torch.cuda.synchronize()
+    one, zero = np.array([1.0, 0, 0, 0]), np.zeros(4)
+    refW = qsynth.empty(k, n)
+    from oracle import oracle as orc
+    orc.qgemm("H", "N", k, n, mb, one, Xs, dYs, zero, refW)
+    refX = qsynth.empty(mb, k)
+    orc.qgemm("N", "H", mb, k, n, one, dYs, Ws, zero, refX)
+    assert rel_fro(dW.cpu().numpy(), refW) <= TOL
+    assert rel_fro(dX.cpu().numpy(), refX) <= TOL
