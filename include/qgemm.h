@@ -300,7 +300,8 @@ int qherk(int uplo, int trans, int64_t n, int64_t k, double alpha,
           void *C, int64_t ldc, int64_t psC, int layout, int precision,
           void *workspace, size_t workspace_bytes, void *stream);
 
-/* Workspace qherk() needs (0 for QGEMM_FP64). */
+/* Workspace qherk() needs; for QGEMM_FP64 the optional one that lets an
+ * update with few tiles in its triangle and a long k split K (as qgemm). */
 size_t qherk_workspace_bytes(int uplo, int trans, int64_t n, int64_t k,
                              int layout, int precision);
 

@@ -263,9 +263,16 @@ int qherk(int uplo, int trans, int64_t n, int64_t k, double alpha, const void *A
 
 size_t qherk_workspace_bytes(int uplo, int trans, int64_t n, int64_t k, int layout,
                              int precision) {
-  (void)uplo;
   if (trans != QGEMM_OP_N && trans != QGEMM_OP_H) return 0;
-  if (precision == QGEMM_FP64) return 0;  // a triangle is never split along K
+  if (precision == QGEMM_FP64) {  // optional: lets a small-n, long-k update split K
+    if ((uplo != QGEMM_LOWER && uplo != QGEMM_UPPER) || n <= 0 || k <= 0) return 0;
+    if (layout != QGEMM_INTERLEAVED && layout != QGEMM_SPLIT_PLANES) return 0;
+    GemmDesc d{};
+    d.m = d.n = n;
+    d.k = k;
+    d.tri = uplo == QGEMM_LOWER ? 1 : 2;
+    return fp64_splitk_bytes(n, n, fp64_ksplit(d, device_sms()));
+  }
   return qgemm_workspace_bytes(trans, trans == QGEMM_OP_N ? QGEMM_OP_H : QGEMM_OP_N, n, n, k,
                                layout, precision);
 }

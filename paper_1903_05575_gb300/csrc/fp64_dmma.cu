@@ -68,16 +68,20 @@ __global__ void __launch_bounds__(kThreads)
 
 // K split: P = sum over z of the partial products (z ascending, so the result
 // does not depend on the order the CTAs finished), then C <- alpha P + beta C
-// with left products in FP64; beta == 0 does not read C.
+// with left products in FP64; beta == 0 does not read C.  tri: only the
+// stored triangle (1 lower, 2 upper), its diagonal real (Hermitian update).
 template <int LAYOUT>
 __global__ void __launch_bounds__(256)
     splitk_reduce_kernel(const double *__restrict__ part, int ksplit, int64_t m, int64_t n,
                          double *C, int64_t ldc, int64_t psC, double a0, double a1, double a2,
-                         double a3, double b0, double b1, double b2, double b3, int beta_zero) {
+                         double a3, double b0, double b1, double b2, double b3, int beta_zero,
+                         int tri) {
   const double al[4] = {a0, a1, a2, a3}, be[4] = {b0, b1, b2, b3};
   const int64_t total = m * n, slab = total * 4;
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e % m, j = e / m;
+    if ((tri == 1 && i < j) || (tri == 2 && i > j)) continue;
     double P[4] = {0.0, 0.0, 0.0, 0.0};
     for (int z = 0; z < ksplit; ++z) {
       const double2 *q = reinterpret_cast<const double2 *>(part + z * slab + 4 * e);
@@ -87,7 +91,6 @@ __global__ void __launch_bounds__(256)
       P[2] += hi.x;
       P[3] += hi.y;
     }
-    const int64_t i = e % m, j = e / m;
     double *q[4];
 #pragma unroll
     for (int s = 0; s < 4; ++s)
@@ -107,7 +110,7 @@ __global__ void __launch_bounds__(256)
         v = fma(sg * al[s], P[j2], v);
         if (!beta_zero) v = fma(sg * be[s], c[j2], v);
       }
-      *q[cc] = v;
+      *q[cc] = (tri && i == j && cc != 0) ? 0.0 : v;
     }
   }
 }
@@ -260,10 +263,14 @@ int launch_keyed(int key, const CUtensorMap &tmA, const CUtensorMap &tmB, const 
 // C of fewer than 8 waves of tiles, take the fewest shares s in [2, 256]
 // whose fraction is within 2 % of the best, keeping at least 8 k-blocks (128
 // quaternion k) per share, and split only when the best gains 5 % over s = 1.
-// Plain products only (no triangle, k-range or turned-around problem).
+// Plain products and the Hermitian update's triangle (whose tiles outside
+// the triangle exit at once and do not count); no k-range (triangular
+// operand) or turned-around problem.
 int fp64_ksplit(const GemmDesc &d, int sms) {
-  if (d.tri || d.krange || d.swap || d.kwidth != 4 || d.m <= 0 || d.n <= 0) return 1;
-  const int64_t tiles = ((d.m + 15) / 16) * ((d.n + 15) / 16);
+  if (d.krange || d.swap || d.kwidth != 4 || d.m <= 0 || d.n <= 0) return 1;
+  const int64_t tm = (d.m + 15) / 16, tn = (d.n + 15) / 16;
+  // a square triangle keeps tm (tm + 1) / 2 of its tm^2 tiles
+  const int64_t tiles = (d.tri && tm == tn) ? tm * (tm + 1) / 2 : tm * tn;
   const int64_t slots = 2LL * sms;
   if (tiles >= 8 * slots) return 1;
   const int64_t ktiles = (d.k + kBKQ - 1) / kBKQ;
@@ -346,11 +353,11 @@ int launch_fp64_gemm_ws(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream
   if (d.layout == QGEMM_INTERLEAVED)
     splitk_reduce_kernel<QGEMM_INTERLEAVED><<<static_cast<unsigned>(blocks), 256, 0, stream>>>(
         a.op.part, ks, d.m, d.n, C, d.ldc, d.psc, al[0], al[1], al[2], al[3], be[0], be[1],
-        be[2], be[3], d.beta_zero ? 1 : 0);
+        be[2], be[3], d.beta_zero ? 1 : 0, d.tri);
   else
     splitk_reduce_kernel<QGEMM_SPLIT_PLANES><<<static_cast<unsigned>(blocks), 256, 0, stream>>>(
         a.op.part, ks, d.m, d.n, C, d.ldc, d.psc, al[0], al[1], al[2], al[3], be[0], be[1],
-        be[2], be[3], d.beta_zero ? 1 : 0);
+        be[2], be[3], d.beta_zero ? 1 : 0, d.tri);
   return launch_status();
 }
 

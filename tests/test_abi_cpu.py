@@ -89,13 +89,15 @@ def test_fp64_split_k_workspace():
     SMs without a device), the fewest shares s in [2, min(256, k-blocks / 8)]
     whose busy fraction (CTAs over whole waves) is within 2 % of the best, if
     the best gains 5 % over s = 1; s partial products of 32 bytes per
-    quaternion.  0 when
-    nothing is split, and for the Hermitian update (a triangle is never
-    split)."""
+    quaternion; 0 when nothing is split.  The Hermitian update counts only
+    the tiles that meet its triangle."""
     L = _abi.lib()
 
-    def expect(m, n, k, sms=152):
+    def expect(m, n, k, sms=152, tri=False):
         tiles = -(-m // 16) * -(-n // 16)
+        if tri:                      # tiles meeting the triangle of a square C
+            t = -(-n // 16)
+            tiles = t * (t + 1) // 2
         slots = 2 * sms
         if tiles >= 8 * slots:
             return 0
@@ -113,7 +115,10 @@ def test_fp64_split_k_workspace():
         assert L.qgemm_workspace_bytes(0, 0, m, n, k, 0, 0) == expect(m, n, k), (m, n, k)
     assert L.qgemm_workspace_bytes(0, 0, 64, 64, 20000, 0, 0) > 0
     assert L.qgemm_workspace_bytes(0, 0, 256, 256, 65536, 0, 0) > 0
-    assert L.qherk_workspace_bytes(0, 0, 64, 20000, 0, 0) == 0
+    for (n, k) in ((64, 20000), (200, 50000), (1000, 4096), (30, 100)):
+        for uplo in (0, 1):
+            assert L.qherk_workspace_bytes(uplo, 0, n, k, 0, 0) == expect(n, n, k, tri=True)
+    assert L.qherk_workspace_bytes(0, 0, 64, 20000, 0, 0) > 0
     # the FP64 call itself never asks for it: no -19 / -20 without a workspace
     assert _call(m=64, n=64, k=20000, lda=64, ldb=20000, ldc=64, A=64, B=64,
                  C=64) in (0, _abi.ERR_NO_DEVICE)

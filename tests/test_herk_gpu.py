@@ -91,3 +91,24 @@ def test_herk_sampled_4096_split():
     err = rel_fro(G[lo, hi], ref)
     print("herk 4096 split sampled rel err %.3e" % err)
     assert err <= 2e-6
+
+
+@pytest.mark.parametrize("layout", qsynth.LAYOUTS)
+@pytest.mark.parametrize("uplo", ["L", "U"])
+@pytest.mark.parametrize("trans", ["N", "H"])
+def test_herk_fp64_split_k(uplo, trans, layout):
+    """A small, long update (n = 50, k = 8000): qherk_workspace_bytes lets
+    the FP64 path split K; the triangle, the real diagonal and the untouched
+    other triangle hold as unsplit."""
+    assert _abi.lib().qherk_workspace_bytes(0 if uplo == "L" else 1, 0 if trans == "N" else 3,
+                                            50, 8000, _abi.LAYOUT[layout], 0) > 0
+    err, _, _ = run(uplo, trans, 50, 8000, layout, torch.float64, 50)
+    assert err <= 1e-12
+
+
+@pytest.mark.parametrize("uplo", ["L", "U"])
+def test_herk_fp64_split_k_small_int_exact(uplo):
+    _, G, R = run(uplo, "H", 37, 3000, "interleaved", torch.float64, 60, alpha=2.0, beta=3.0,
+                  kind="int")
+    tri = np.tril(np.ones((37, 37), bool)) if uplo == "L" else np.triu(np.ones((37, 37), bool))
+    assert np.array_equal(G[tri], R[tri])
