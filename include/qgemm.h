@@ -383,7 +383,8 @@ int qgemm_backward(int64_t mb, int64_t k, int64_t n,
                    int accumulate, int layout, int precision,
                    void *workspace, size_t workspace_bytes, void *stream);
 
-/* Workspace qgemm_backward() needs (the larger of its two products). */
+/* Workspace qgemm_backward() needs (the larger of its two products; for
+ * QGEMM_FP64 the optional one that lets a product split K, as qgemm). */
 size_t qgemm_backward_workspace_bytes(int64_t mb, int64_t k, int64_t n,
                                       int layout, int precision);
 
