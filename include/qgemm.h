@@ -60,7 +60,11 @@
  *                          their small entries).  A row or column holding Inf
  *                          or NaN gives NaN in the matching row or column of
  *                          the product.  Needs a workspace; k <= 2^21
- *                          (QGEMM_ERR_UNSUPPORTED above).
+ *                          (QGEMM_ERR_UNSUPPORTED above).  The size that
+ *                          qgemm_workspace_bytes() reports may exceed the
+ *                          minimum: the rest lets a product with few tiles
+ *                          of C and a long k split K across CTAs (as
+ *                          QGEMM_FP64; without it the call runs unsplit).
  *
  * Memory and streams: every matrix pointer is a DEVICE pointer owned by the
  * caller; alpha and beta are HOST arrays of 4 doubles, read during the call

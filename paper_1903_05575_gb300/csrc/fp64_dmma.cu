@@ -346,18 +346,22 @@ int launch_fp64_gemm_ws(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream
   const int key = (small ? 8 : 0) | (d.layout << 2) | (ta << 1) | tb;
   const int rc = launch_keyed(key, tmA, tmB, a, grid, stream);
   if (rc || ks == 1) return rc;
+  return launch_splitk_reduce(d, a.op.part, ks, stream);
+}
+
+int launch_splitk_reduce(const GemmDesc &d, const double *part, int ks, cudaStream_t stream) {
   const int64_t total = d.m * d.n;
   const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152LL * 16);
   double *C = static_cast<double *>(d.C);
   const double *al = d.alpha, *be = d.beta;
   if (d.layout == QGEMM_INTERLEAVED)
     splitk_reduce_kernel<QGEMM_INTERLEAVED><<<static_cast<unsigned>(blocks), 256, 0, stream>>>(
-        a.op.part, ks, d.m, d.n, C, d.ldc, d.psc, al[0], al[1], al[2], al[3], be[0], be[1],
-        be[2], be[3], d.beta_zero ? 1 : 0, d.tri);
+        part, ks, d.m, d.n, C, d.ldc, d.psc, al[0], al[1], al[2], al[3], be[0], be[1], be[2],
+        be[3], d.beta_zero ? 1 : 0, d.tri);
   else
     splitk_reduce_kernel<QGEMM_SPLIT_PLANES><<<static_cast<unsigned>(blocks), 256, 0, stream>>>(
-        a.op.part, ks, d.m, d.n, C, d.ldc, d.psc, al[0], al[1], al[2], al[3], be[0], be[1],
-        be[2], be[3], d.beta_zero ? 1 : 0, d.tri);
+        part, ks, d.m, d.n, C, d.ldc, d.psc, al[0], al[1], al[2], al[3], be[0], be[1], be[2],
+        be[3], d.beta_zero ? 1 : 0, d.tri);
   return launch_status();
 }
 

@@ -89,6 +89,11 @@ struct SlicedParams {
   double alpha[4], beta[4];
   const int *eA;  // per quaternion row of op(A)
   const int *eB;  // per quaternion column of op(B)
+  // K split (single problems): tile t of the launch is share z = t / (num_mt
+  // num_nt) of its tile's k-blocks, whose product P goes to part + z m n 4
+  // (dense, interleaved, leading dimension m) for a second kernel to sum.
+  int ksplit;     // 0 or 1: no split
+  double *part;
 };
 
 // Pre-pass arguments of one operand.
@@ -170,7 +175,8 @@ __device__ __forceinline__ void tile_coords(const SlicedParams &g, int t, int &m
 
 // k-blocks [lo, hi) of tile (mt, nt): all of K, or the part where a
 // triangular operand can be nonzero for the tile's rows or columns.
-__device__ __forceinline__ void kb_range(const SlicedParams &g, int mt, int nt, int &lo, int &hi) {
+__device__ __forceinline__ void kb_range(const SlicedParams &g, int mt, int nt, int z, int &lo,
+                                         int &hi) {
   lo = 0;
   hi = g.num_kb;
   const int64_t rq0 = static_cast<int64_t>(mt) * SBM, cq0 = static_cast<int64_t>(nt) * SBNQ;
@@ -185,6 +191,12 @@ __device__ __forceinline__ void kb_range(const SlicedParams &g, int mt, int nt, 
     if (e < hi) hi = static_cast<int>(e);
   }
   if (lo > hi) lo = hi;
+  if (g.ksplit > 1) {  // share z of the k-blocks
+    const int64_t span = hi - lo;
+    const int l2 = lo + static_cast<int>(span * z / g.ksplit);
+    hi = lo + static_cast<int>(span * (z + 1) / g.ksplit);
+    lo = l2;
+  }
 }
 
 __device__ __forceinline__ bool tile_skip(const SlicedParams &g, int mt, int nt) {
@@ -302,7 +314,7 @@ __device__ __forceinline__ double scale2(double x, int e) {
 // TMEM columns, P = 2^(e_i + e_n - 38) S, C <- alpha P + beta C in FP64.
 // All lanes execute the TMEM load; the rest is per lane.
 __device__ __forceinline__ void epilogue_piece(const SlicedParams &g, uint32_t spare, int64_t i,
-                                               int ea, int64_t nq0, int q) {
+                                               int ea, int64_t nq0, int q, int z) {
   uint32_t r[8];
   tmem_ld8(spare + 8 * q, r);
   const int64_t nn = nq0 + q;
@@ -318,6 +330,12 @@ __device__ __forceinline__ void epilogue_piece(const SlicedParams &g, uint32_t s
       P[c] = (ea == kNonFinite || eb == kNonFinite) ? __longlong_as_double(0x7ff8000000000000ll)
                                                     : scale2(Sc, ea + eb - 38);
     }
+  }
+  if (g.ksplit > 1) {  // this K share's product, for the summing kernel
+    double *dst = g.part + (static_cast<int64_t>(z) * g.m * g.n + i + nn * g.m) * 4;
+    *reinterpret_cast<double2 *>(dst) = make_double2(P[0], P[1]);
+    *reinterpret_cast<double2 *>(dst + 2) = make_double2(P[2], P[3]);
+    return;
   }
   // element (ci, cj) of C; a transposed problem holds (AB)^H: take conj(D)^T
   int64_t ci = i, cj = nn;
@@ -399,12 +417,13 @@ struct Pending {
   const SlicedParams *g;
   int64_t i, nq0;
   int ea;
+  int z;     // K share (split problems)
   int done;  // quaternions 0 .. done-1 written; 8 when nothing is pending
 };
 
 __device__ __forceinline__ void run_pending(uint32_t spare, Pending &pd, int upto) {
   while (pd.done < upto) {
-    epilogue_piece(*pd.g, spare, pd.i, pd.ea, pd.nq0, pd.done);
+    epilogue_piece(*pd.g, spare, pd.i, pd.ea, pd.nq0, pd.done, pd.z);
     ++pd.done;
   }
 }
@@ -417,7 +436,7 @@ __device__ __forceinline__ void tile_of(int t, const SlicedParams &single, const
                                         const CUtensorMap *smB, const SlicedProb *probs,
                                         const int4 *tiles, const SlicedParams *&g,
                                         const CUtensorMap *&mA, const CUtensorMap *&mB, int &mt,
-                                        int &nt) {
+                                        int &nt, int &z) {
   if (GROUPED) {
     const int4 e = tiles[t];
     const SlicedProb *pr = probs + e.x;
@@ -426,11 +445,14 @@ __device__ __forceinline__ void tile_of(int t, const SlicedParams &single, const
     mB = &pr->tmB;
     mt = e.y;
     nt = e.z;
+    z = 0;
   } else {
     g = &single;
     mA = smA;
     mB = smB;
-    tile_coords(single, t, mt, nt);
+    const int per = single.num_mt * single.num_nt;
+    z = single.ksplit > 1 ? t / per : 0;
+    tile_coords(single, single.ksplit > 1 ? t % per : t, mt, nt);
   }
 }
 
@@ -477,11 +499,11 @@ __global__ void __launch_bounds__(kSThreads, 1)
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const SlicedParams *g;
         const CUtensorMap *mA, *mB;
-        int mt, nt;
-        tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt);
+        int mt, nt, z;
+        tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt, z);
         if (tile_skip(*g, mt, nt)) continue;
         int kb_lo, kb_hi;
-        kb_range(*g, mt, nt, kb_lo, kb_hi);
+        kb_range(*g, mt, nt, z, kb_lo, kb_hi);
         for (int kb = kb_lo; kb < kb_hi; ++kb, ++s_run) {
           const int st = s_run % SST;
           if (!wait_phase(&ctl->empty[st], ((s_run / SST) & 1) ^ 1, limit_ns, ctl)) {
@@ -514,11 +536,11 @@ __global__ void __launch_bounds__(kSThreads, 1)
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const SlicedParams *g;
         const CUtensorMap *mA, *mB;
-        int mt, nt;
-        tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt);
+        int mt, nt, z;
+        tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt, z);
         if (tile_skip(*g, mt, nt)) continue;
         int kb_lo, kb_hi;
-        kb_range(*g, mt, nt, kb_lo, kb_hi);
+        kb_range(*g, mt, nt, z, kb_lo, kb_hi);
         const int nch = (kb_hi - kb_lo + kChunkKb - 1) / kChunkKb;
         if (nch > 0) {
           // levels 4, 5 of the previous tile read
@@ -594,15 +616,15 @@ __global__ void __launch_bounds__(kSThreads, 1)
     const uint32_t spare = tmem + lanes + 6 * SBN + 64 * half;
     uint32_t c_run = 0;
     bool ok = true;
-    Pending pd{nullptr, 0, 0, 0, 8};
+    Pending pd{nullptr, 0, 0, 0, 0, 8};
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       const SlicedParams *g;
       const CUtensorMap *mA, *mB;
-      int mt, nt;
-      tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt);
+      int mt, nt, z;
+      tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt, z);
       if (tile_skip(*g, mt, nt)) continue;
       int kb_lo, kb_hi;
-      kb_range(*g, mt, nt, kb_lo, kb_hi);
+      kb_range(*g, mt, nt, z, kb_lo, kb_hi);
       const int nch = (kb_hi - kb_lo + kChunkKb - 1) / kChunkKb;
       const int nbound = nch - 1;  // chunk ends before the tile's last
       long long T[32];
@@ -697,6 +719,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
       pd.i = static_cast<int64_t>(mt) * SBM + 32 * quad + lane;
       pd.nq0 = static_cast<int64_t>(nt) * SBNQ + 8 * half;
       pd.ea = pd.i < g->m ? g->eA[pd.i] : 0;
+      pd.z = z;
       pd.done = 0;
     }
     run_pending(spare, pd, 8);
@@ -1110,11 +1133,46 @@ int sm_count() {
   return sms > 0 ? sms : 1;
 }
 
+// K shares of a single problem (one CTA per SM, tiles of SBM x SBNQ
+// quaternions): when C has fewer than 8 waves of tiles, the fewest shares s in
+// [2, 256] whose tiles x s CTAs fill their waves to within 2 % of the best s,
+// with at least 32 k-blocks (256 quaternion k, 4 chunks) per share, if the
+// best beats s = 1 by 5 %.  Plain products only (no triangle, k-range or
+// turned-around problem).  1: no split.
+int sliced_ksplit(const GemmDesc &d, int sms) {
+  if (d.tri || d.krange || d.swap || d.m <= 0 || d.n <= 0 || d.k <= 0) return 1;
+  const int64_t tiles = ((d.m + SBM - 1) / SBM) * ((d.n + SBNQ - 1) / SBNQ);
+  const int64_t slots = sms;
+  if (tiles >= 8 * slots) return 1;
+  const int64_t num_kb = ((d.kwidth * d.k + SBK - 1) / SBK * SBK) / SBK;
+  const int64_t smax = std::min<int64_t>(256, num_kb / 32);
+  auto busy = [&](int64_t s) {
+    const int64_t ctas = tiles * s;
+    const int64_t waves = (ctas + slots - 1) / slots;
+    return static_cast<double>(ctas) / static_cast<double>(waves * slots);
+  };
+  double top = busy(1);
+  for (int64_t s = 2; s <= smax; ++s) top = std::max(top, busy(s));
+  if (top < busy(1) + 0.05) return 1;
+  for (int64_t s = 2; s <= smax; ++s)
+    if (busy(s) >= top - 0.02) return static_cast<int>(s);
+  return 1;
+}
+
 }  // namespace
 
+// Required: the slices, maxima and exponents (plan_for).
 int sliced_workspace_bytes(const GemmDesc &d, size_t *bytes) {
   *bytes = (d.k == 0 || d.m == 0 || d.n == 0) ? 0 : plan_for(d).total;
   return QGEMM_SUCCESS;
+}
+
+// Optional, after the required part: the K shares' partial products of a
+// product that splits K (0 when it does not).
+size_t sliced_splitk_bytes(const GemmDesc &d) {
+  if (d.k == 0 || d.m == 0 || d.n == 0) return 0;
+  const int ks = sliced_ksplit(d, device_sms());
+  return ks > 1 ? static_cast<size_t>(ks) * d.m * d.n * 32 : 0;
 }
 
 int launch_sliced_gemm(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_t stream) {
@@ -1149,15 +1207,30 @@ int launch_sliced_gemm(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_
   std::memset(&tmB, 0, sizeof(tmB));
   if (!encode_slices(&tmA, wa, pl.kp, d.m, SBM) || !encode_slices(&tmB, wb, pl.kp, 4 * d.n, SBN))
     return QGEMM_ERR_UNSUPPORTED;
-  const SlicedParams g = params_for(d, pl.kp, ea, eb);
-  const int64_t tiles = static_cast<int64_t>(g.num_mt) * g.num_nt;
+  SlicedParams g = params_for(d, pl.kp, ea, eb);
+  // K shares: as many as chosen for this device that fit after the plan
+  int ks = sliced_ksplit(d, sm_count());
+  if (ks > 1) {
+    const size_t per = static_cast<size_t>(d.m) * d.n * 32;
+    const int64_t fit = static_cast<int64_t>((ws_bytes - pl.total) / per);
+    if (fit < ks) ks = static_cast<int>(fit);
+    if (ks > 1) {
+      g.ksplit = ks;
+      g.part = reinterpret_cast<double *>(w + pl.total);
+    } else {
+      ks = 1;
+    }
+  }
+  const int64_t tiles = static_cast<int64_t>(g.num_mt) * g.num_nt * ks;
   if (tiles > 0x7fffffff) return QGEMM_ERR_UNSUPPORTED;
   rc = set_gemm_smem<false>();
   if (rc) return rc;
   const int grid = static_cast<int>(std::min<int64_t>(tiles, sm_count()));
   sliced_gemm_kernel<false><<<grid, kSThreads, kSmem, stream>>>(
       tmA, tmB, g, nullptr, nullptr, static_cast<int>(tiles), wait_limit_ns());
-  return launch_status();
+  rc = launch_status();
+  if (rc || ks == 1) return rc;
+  return launch_splitk_reduce(d, g.part, ks, stream);
 }
 
 // ---------------------------------------------------- grouped batches ---

@@ -78,6 +78,10 @@ int launch_fp64_gemm_ws(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream
 int fp64_ksplit(const GemmDesc &d, int sms);
 size_t fp64_splitk_bytes(int64_t m, int64_t n, int ksplit);
 int device_sms();  // SM count of the current device (152 when there is none)
+// C <- alpha (sum over z < ks of the partial products in part) + beta C in FP64
+// for an FP64 C (d's layout, scalars and triangle); part: ks dense slabs of
+// m n interleaved quaternions, summed in z order.
+int launch_splitk_reduce(const GemmDesc &d, const double *part, int ks, cudaStream_t stream);
 int launch_fp64_mixed(const GemmDesc &d, cudaStream_t stream);
 int launch_scale(const GemmDesc &d, bool fp64, cudaStream_t stream);
 int launch_herk_scale(const GemmDesc &d, bool fp64, cudaStream_t stream);
@@ -85,6 +89,9 @@ int split_workspace_bytes(const GemmDesc &d, size_t *bytes);
 int launch_split_gemm(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_t stream);
 int noalloc_scratch(void **out);
 int sliced_workspace_bytes(const GemmDesc &d, size_t *bytes);
+// Optional workspace after sliced_workspace_bytes() that lets a single
+// digit-sliced product split K (0 when it would not).
+size_t sliced_splitk_bytes(const GemmDesc &d);
 int launch_sliced_gemm(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_t stream);
 int validate_gemm(int opA, int opB, int64_t m, int64_t n, int64_t k, const double *alpha,
                   const void *A, int64_t lda, int64_t psA, const void *B, int64_t ldb,

@@ -247,3 +247,104 @@ def test_real_and_quaternion_scalars(scalars):
     16-product Hamilton form; both against the oracle."""
     al, be = (np.array(x) for x in scalars)
     check("N", "H", 140, 33, 90, "interleaved", seed=901, alpha=al, beta=be)
+
+
+# ---------------------------------------------------------------- K split ---
+def sliced_split_shares(m, n, k, sms):
+    """Shares the digit-sliced path splits a single product into (tiles of
+    128 x 16 quaternions, one CTA per SM, >= 32 k-blocks of 32 reals each)."""
+    tiles = -(-m // 128) * -(-n // 16)
+    if tiles >= 8 * sms:
+        return 1
+    num_kb = -(-4 * k // 32)
+
+    def busy(s):
+        return tiles * s / (-(-tiles * s // sms) * sms)
+    shares = range(2, min(256, num_kb // 32) + 1)
+    top = max([busy(1)] + [busy(s) for s in shares])
+    if top < busy(1) + 0.05:
+        return 1
+    return min(s for s in shares if busy(s) >= top - 0.02)
+
+
+SPLIT_SHAPES = [(64, 64, 20000), (37, 29, 3000), (130, 70, 4000), (1, 1, 10000)]
+
+
+@pytest.mark.parametrize("layout", qsynth.LAYOUTS)
+@pytest.mark.parametrize("shape", SPLIT_SHAPES)
+@pytest.mark.parametrize("ops_pair", [("N", "N"), ("H", "N"), ("T", "C")])
+def test_split_k_parity(ops_pair, shape, layout):
+    """Few tiles of C, long k: the K shares' partial products are summed by a
+    second kernel; every entry stays within the bound, the Frobenius error
+    within 1e-12."""
+    m, n, k = shape
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert sliced_split_shares(m, n, k, sms) > 1
+    check(ops_pair[0], ops_pair[1], m, n, k, layout, seed=m + n + k % 997)
+
+
+def test_split_k_small_int_exact():
+    check("N", "H", 37, 29, 3000, "interleaved", seed=7100, kind="int",
+          alpha=np.array([1.0, -2.0, 0.0, 1.0]), beta=np.array([2.0, 0, 1.0, -1.0]))
+
+
+def test_split_k_beta_zero_and_non_finite():
+    """beta = 0 with NaN in C (not read), a NaN row of A and an Inf column of
+    B: that row and column of C are NaN after the shares are summed."""
+    m, n, k = 40, 24, 5000
+    A, B, C = make_case("N", "N", m, n, k, "interleaved", 7200)
+    A2, B2 = A.copy(), B.copy()
+    A[7, 3, 2] = np.nan
+    B[5, 11, 0] = np.inf
+    ref = qsynth.components(oracle_full("N", "N", m, n, k, ALPHA, A2, B2, np.zeros(4), C,
+                                        "interleaved"), m, "interleaved")
+    C[:, :m] = np.nan
+    got = run("N", "N", m, n, k, ALPHA, A, B, np.zeros(4), C, "interleaved")
+    g = qsynth.components(got, m, "interleaved")
+    assert np.isnan(g[3, :, :]).all() and np.isnan(g[:, 5, :]).all()
+    mask = np.ones((m, n), bool)
+    mask[3, :] = False
+    mask[:, 5] = False
+    assert rel_fro(g[mask], ref[mask]) <= TOL
+
+
+def test_split_k_optional_part_and_speed():
+    """The minimum workspace runs K unsplit, the reported one splits it: same
+    results within the bound, and the split run much faster (4 tiles of C
+    leave 148 SMs idle unsplit)."""
+    from paper_1903_05575_gb300 import _abi
+    m, n, k = 64, 64, 32768
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ks = sliced_split_shares(m, n, k, sms)
+    assert ks > 1
+    L = _abi.lib()
+    full = L.qgemm_workspace_bytes(0, 0, m, n, k, 0, 2)
+    need_min = full - ks * m * n * 32
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(73)
+    A = torch.randn((k, m, 4), dtype=torch.float64, device="cuda", generator=gen)
+    B = torch.randn((n, k, 4), dtype=torch.float64, device="cuda", generator=gen)
+    ws = torch.empty(full, dtype=torch.uint8, device="cuda")
+    one, zero = _abi.q4([1, 0, 0, 0]), _abi.q4([0, 0, 0, 0])
+    stream = torch.cuda.current_stream().cuda_stream
+    outs, times = [], []
+    for wb in (full, need_min):
+        C = torch.zeros((n, m, 4), dtype=torch.float64, device="cuda")
+
+        def call():
+            _abi.check(L.qgemm(0, 0, m, n, k, one, A.data_ptr(), m, 0, B.data_ptr(), k, 0,
+                               zero, C.data_ptr(), m, 0, 0, 2, ws.data_ptr(), wb, stream))
+        call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        call()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        outs.append(C.cpu().numpy())
+    assert L.qgemm(0, 0, m, n, k, one, A.data_ptr(), m, 0, B.data_ptr(), k, 0, zero,
+                   C.data_ptr(), m, 0, 0, 2, ws.data_ptr(), need_min - 1, stream) == -20
+    print("split %.2f ms, unsplit %.2f ms" % tuple(times))
+    assert rel_fro(outs[0], outs[1]) <= 1e-13
+    assert times[0] * 3 < times[1]
