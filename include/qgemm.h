@@ -42,7 +42,10 @@
  *                          accumulation in tensor memory, drained in K-chunks
  *                          into a higher-precision accumulator; alpha and beta
  *                          are applied in FP64 and the result is rounded once
- *                          to float.  Needs a workspace (qgemm_workspace_bytes).
+ *                          to float.  Needs a workspace (qgemm_workspace_bytes;
+ *                          beyond its minimum, the size reported lets a
+ *                          product with few tiles of C and a long k split K
+ *                          across CTAs, as QGEMM_FP64).
  *   QGEMM_FP64_SLICED_BF16: double data; FP64-class result on the BF16 tensor
  *                          cores (no paper counterpart; the paper is FP64
  *                          throughout, and GB300's FP64 pipe is narrow).  Each

@@ -221,8 +221,12 @@ size_t qgemm_workspace_bytes(int opA, int opB, int64_t m, int64_t n, int64_t k, 
   if (precision == QGEMM_FP64) return fp64_splitk_bytes(m, n, fp64_ksplit(d, device_sms()));
   size_t b = 0;
   if (workspace_need(d, precision, &b)) return 0;
-  // digit-sliced: required part, then the optional K shares
+  // tensor-core paths: the required part, then the optional K shares
   if (precision == QGEMM_FP64_SLICED_BF16 && b > 0) b += sliced_splitk_bytes(d);
+  if (precision == QGEMM_FP32_SPLIT_BF16 && b > 0) {
+    const size_t extra = split_splitk_bytes(d);
+    if (extra > 0) b = (b + 255) / 256 * 256 + extra;
+  }
   return b;
 }
 

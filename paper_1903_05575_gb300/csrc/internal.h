@@ -92,6 +92,9 @@ int sliced_workspace_bytes(const GemmDesc &d, size_t *bytes);
 // Optional workspace after sliced_workspace_bytes() that lets a single
 // digit-sliced product split K (0 when it would not).
 size_t sliced_splitk_bytes(const GemmDesc &d);
+// Optional workspace after split_workspace_bytes() (rounded up to 256 bytes)
+// that lets a single split-BF16 product split K (0 when it would not).
+size_t split_splitk_bytes(const GemmDesc &d);
 int launch_sliced_gemm(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_t stream);
 int validate_gemm(int opA, int opB, int64_t m, int64_t n, int64_t k, const double *alpha,
                   const void *A, int64_t lda, int64_t psA, const void *B, int64_t ldb,

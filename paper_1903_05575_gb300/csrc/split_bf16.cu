@@ -243,7 +243,85 @@ int launch_fused_single(const GemmDesc &d, const CUtensorMap &tmA, const CUtenso
   return launch_status();
 }
 
+// K split: P = sum over z of the FP32 partial products (in FP64, z
+// ascending), then C <- alpha P + beta C with left products in FP64 and one
+// rounding to float; beta == 0 does not read C.
+template <int LAYOUT>
+__global__ void __launch_bounds__(256)
+    split_reduce_kernel(const float *__restrict__ part, int ksplit, int64_t m, int64_t n,
+                        float *C, int64_t ldc, int64_t psC, double a0, double a1, double a2,
+                        double a3, double b0, double b1, double b2, double b3, int beta_zero) {
+  const double al[4] = {a0, a1, a2, a3}, be[4] = {b0, b1, b2, b3};
+  const int64_t total = m * n, slab = total * 4;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    double P[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int z = 0; z < ksplit; ++z) {
+      const float4 v = *reinterpret_cast<const float4 *>(part + z * slab + 4 * e);
+      P[0] += v.x;
+      P[1] += v.y;
+      P[2] += v.z;
+      P[3] += v.w;
+    }
+    const int64_t i = e % m, j = e / m;
+    float *q[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+      q[s] = LAYOUT == QGEMM_INTERLEAVED ? C + 4 * (i + j * ldc) + s : C + s * psC + i + j * ldc;
+    double c[4] = {0.0, 0.0, 0.0, 0.0};
+    if (!beta_zero) {
+#pragma unroll
+      for (int s = 0; s < 4; ++s) c[s] = *q[s];
+    }
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      double v = 0.0;
+#pragma unroll
+      for (int j2 = 0; j2 < 4; ++j2) {
+        const int s = cc ^ j2;
+        const double sg = basis_sign(s, j2) < 0 ? -1.0 : 1.0;
+        v = fma(sg * al[s], P[j2], v);
+        if (!beta_zero) v = fma(sg * be[s], c[j2], v);
+      }
+      *q[cc] = static_cast<float>(v);
+    }
+  }
+}
+
+// K shares of a single problem (one CTA per SM, tiles of BM x BNQ
+// quaternions): when C has fewer than 8 waves of tiles, the fewest shares s in
+// [2, 256] whose tiles x s CTAs fill their waves to within 2 % of the best s,
+// with at least 64 k-blocks (512 quaternion k) per share, if the best beats
+// s = 1 by 5 %.  Plain products only (no triangle, k-range or turned-around
+// problem).  1: no split.
+int split_ksplit(const GemmDesc &d, int sms) {
+  if (d.tri || d.krange || d.swap || d.m <= 0 || d.n <= 0 || d.k <= 0) return 1;
+  const int64_t tiles = ((d.m + BM - 1) / BM) * ((d.n + BNQ - 1) / BNQ);
+  const int64_t slots = sms;
+  if (tiles >= 8 * slots) return 1;
+  const int64_t num_kb = (d.kwidth * d.k + BK - 1) / BK;
+  const int64_t smax = std::min<int64_t>(256, num_kb / 64);
+  auto busy = [&](int64_t s) {
+    const int64_t ctas = tiles * s;
+    const int64_t waves = (ctas + slots - 1) / slots;
+    return static_cast<double>(ctas) / static_cast<double>(waves * slots);
+  };
+  double top = busy(1);
+  for (int64_t s = 2; s <= smax; ++s) top = std::max(top, busy(s));
+  if (top < busy(1) + 0.05) return 1;
+  for (int64_t s = 2; s <= smax; ++s)
+    if (busy(s) >= top - 0.02) return static_cast<int>(s);
+  return 1;
+}
+
 }  // namespace
+
+size_t split_splitk_bytes(const GemmDesc &d) {
+  if (d.k == 0 || d.m == 0 || d.n == 0) return 0;
+  if (want_fused() && plain_quaternion(d)) return 0;  // the fused kernel never splits
+  const int ks = split_ksplit(d, device_sms());
+  return ks > 1 ? static_cast<size_t>(ks) * d.m * d.n * 16 : 0;
+}
 
 int split_workspace_bytes(const GemmDesc &d, size_t *bytes) {
   if (want_fused() && plain_quaternion(d) && d.k > 0 && d.m > 0 && d.n > 0) {
@@ -285,17 +363,45 @@ int launch_split_gemm(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_t
   if (!encode_bf16_3d(&tmA, wa, pl.kp, d.m, BM) || !encode_bf16_3d(&tmB, wb, pl.kp, 4 * d.n, BN))
     return QGEMM_ERR_UNSUPPORTED;
   GemmParams g = gemm_params(d, pl.kp);
-  const int64_t tiles = static_cast<int64_t>(g.num_mt) * g.num_nt;
-  if (tiles > 0x7fffffff) return QGEMM_ERR_UNSUPPORTED;
-  rc = set_smem(gemm_kernel<SplitErr, false>, kSmemBytes);
-  if (rc) return rc;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // K shares: as many as chosen for this device that fit after the plan
+  int ks = split_ksplit(d, sms > 0 ? sms : 1);
+  if (ks > 1) {
+    const size_t per = static_cast<size_t>(d.m) * d.n * 16;
+    const size_t off = (pl.total + 255) / 256 * 256;
+    const int64_t fit = ws_bytes > off ? static_cast<int64_t>((ws_bytes - off) / per) : 0;
+    if (fit < ks) ks = static_cast<int>(fit);
+    if (ks > 1) {
+      g.ksplit = ks;
+      g.part = reinterpret_cast<float *>(static_cast<unsigned char *>(ws) + off);
+    } else {
+      ks = 1;
+    }
+  }
+  const int64_t tiles = static_cast<int64_t>(g.num_mt) * g.num_nt * ks;
+  if (tiles > 0x7fffffff) return QGEMM_ERR_UNSUPPORTED;
+  rc = set_smem(gemm_kernel<SplitErr, false>, kSmemBytes);
+  if (rc) return rc;
   const int grid = static_cast<int>(std::min<int64_t>(tiles, sms));
   gemm_kernel<SplitErr, false><<<grid, kThreads, kSmemBytes, stream>>>(
       tmA, tmB, g, nullptr, nullptr, static_cast<int>(tiles), chunk_for(g.num_kb),
       wait_limit_ns());
+  rc = launch_status();
+  if (rc || ks == 1) return rc;
+  const int64_t total = d.m * d.n;
+  const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152LL * 16);
+  const double *al = d.alpha, *be = d.beta;
+  float *C = static_cast<float *>(d.C);
+  if (d.layout == QGEMM_INTERLEAVED)
+    split_reduce_kernel<QGEMM_INTERLEAVED><<<static_cast<unsigned>(blocks), 256, 0, stream>>>(
+        g.part, ks, d.m, d.n, C, d.ldc, d.psc, al[0], al[1], al[2], al[3], be[0], be[1], be[2],
+        be[3], d.beta_zero ? 1 : 0);
+  else
+    split_reduce_kernel<QGEMM_SPLIT_PLANES><<<static_cast<unsigned>(blocks), 256, 0, stream>>>(
+        g.part, ks, d.m, d.n, C, d.ldc, d.psc, al[0], al[1], al[2], al[3], be[0], be[1], be[2],
+        be[3], d.beta_zero ? 1 : 0);
   return launch_status();
 }
 

@@ -290,11 +290,18 @@ struct GemmParams {
   int tri;                // 0 full; 1 lower (row >= col) only; 2 upper; real diagonal
   int swap;               // 1: the kernel computed D = (op(A) op(B))^H; store C = conj(D)^T
   int krange;             // k-range of a tile when op(A) or op(B) is triangular (GemmDesc)
+  // K split (single problems): tile t of the launch is share z = t / (num_mt
+  // num_nt) of its tile's k-blocks, whose product P (FP32) goes to part +
+  // z m n 4 (dense, interleaved, leading dimension m) for a second kernel.
+  int ksplit;             // 0 or 1: no split
+  float *part;
 };
 
-// k-blocks [lo, hi) of tile (mt, nt): all of K, or the part where a
-// triangular operand can be nonzero for the tile's rows or columns.
-__host__ __device__ inline void kb_range(const GemmParams &g, int mt, int nt, int &lo, int &hi) {
+// k-blocks [lo, hi) of tile (mt, nt), share z: all of K, or the part where a
+// triangular operand can be nonzero for the tile's rows or columns; then
+// share z of it when the problem splits K.
+__host__ __device__ inline void kb_range(const GemmParams &g, int mt, int nt, int z, int &lo,
+                                         int &hi) {
   lo = 0;
   hi = g.num_kb;
   const int64_t rq0 = static_cast<int64_t>(mt) * BM, cq0 = static_cast<int64_t>(nt) * BNQ;
@@ -309,6 +316,12 @@ __host__ __device__ inline void kb_range(const GemmParams &g, int mt, int nt, in
     if (e < hi) hi = static_cast<int>(e);
   }
   if (lo > hi) lo = hi;
+  if (g.ksplit > 1) {
+    const int64_t span = hi - lo;
+    const int l2 = lo + static_cast<int>(span * z / g.ksplit);
+    hi = lo + static_cast<int>(span * (z + 1) / g.ksplit);
+    lo = l2;
+  }
 }
 
 // Device descriptor of one problem of a grouped batch.
@@ -361,7 +374,7 @@ __device__ __forceinline__ void tile_of(int t, const GemmParams &single, const C
                                         const CUtensorMap *smB, const SplitProb *probs,
                                         const int4 *tiles, const GemmParams *&g,
                                         const CUtensorMap *&mA, const CUtensorMap *&mB, int &mt,
-                                        int &nt) {
+                                        int &nt, int &z) {
   if (GROUPED) {
     const int4 e = tiles[t];
     const SplitProb *pr = probs + e.x;
@@ -370,10 +383,17 @@ __device__ __forceinline__ void tile_of(int t, const GemmParams &single, const C
     mB = &pr->tmB;
     mt = e.y;
     nt = e.z;
+    z = 0;
   } else {
     g = &single;
     mA = smA;
     mB = smB;
+    z = 0;
+    if (single.ksplit > 1) {  // share z of tile t % (tiles of C)
+      const int per = single.num_mt * single.num_nt;
+      z = t / per;
+      t %= per;
+    }
     const int per_group = kGroupM * single.num_nt;
     const int first_m = (t / per_group) * kGroupM;
     const int gsize = min(single.num_mt - first_m, kGroupM);
@@ -493,6 +513,21 @@ __device__ __forceinline__ void epilogue(const GemmParams &g, int64_t i, int64_t
   }
 }
 
+// K split: the product P of share z for row i and the 32 quaternion columns
+// from nbase, stored to the share's slab (dense, interleaved, ld m).
+__device__ __forceinline__ void store_partial(const GemmParams &g, int64_t i, int64_t nbase, int z,
+                                              const float (&acc)[128]) {
+  if (i >= g.m) return;
+  float *slab = g.part + static_cast<int64_t>(z) * g.m * g.n * 4;
+#pragma unroll
+  for (int q = 0; q < 32; ++q) {
+    const int64_t nn = nbase + q;
+    if (nn >= g.n) break;
+    *reinterpret_cast<float4 *>(slab + 4 * (i + nn * g.m)) =
+        make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+  }
+}
+
 // Persistent split-BF16 GEMM.  Single problem: tensor maps and parameters
 // are kernel parameters, tiles rasterised in groups of kGroupM row tiles.
 // Grouped: tiles[t] = (problem, row tile, column tile), per-problem maps and
@@ -539,11 +574,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const GemmParams *g;
         const CUtensorMap *mA, *mB;
-        int mt, nt;
-        tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt);
+        int mt, nt, z;
+        tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt, z);
         if (tile_skip(*g, mt, nt)) continue;
         int kb_lo, kb_hi;
-        kb_range(*g, mt, nt, kb_lo, kb_hi);
+        kb_range(*g, mt, nt, z, kb_lo, kb_hi);
         for (int kb = kb_lo; kb < kb_hi; ++kb, ++s_run) {
           const int st = s_run % STAGES;
           if (!wait_phase(&ctl->empty[st], ((s_run / STAGES) & 1) ^ 1, limit_ns, ctl)) {
@@ -572,11 +607,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const GemmParams *g;
         const CUtensorMap *mA, *mB;
-        int mt, nt;
-        tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt);
+        int mt, nt, z;
+        tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt, z);
         if (tile_skip(*g, mt, nt)) continue;
         int kb_lo, nkb;
-        kb_range(*g, mt, nt, kb_lo, nkb);
+        kb_range(*g, mt, nt, z, kb_lo, nkb);
         for (int kb = kb_lo; kb < nkb && ok; ++c_run) {
           const int b = c_run & 1;
           if (!wait_phase(&ctl->accempty[b], ((c_run >> 1) & 1) ^ 1, limit_ns, ctl)) {
@@ -629,14 +664,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       const GemmParams *g;
       const CUtensorMap *mA, *mB;
-      int mt, nt;
-      tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt);
+      int mt, nt, z;
+      tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt, z);
       if (tile_skip(*g, mt, nt)) continue;
       int kb_lo, kb_hi;
-      kb_range(*g, mt, nt, kb_lo, kb_hi);
+      kb_range(*g, mt, nt, z, kb_lo, kb_hi);
       const int nch = (kb_hi - kb_lo + chunk - 1) / chunk;
-      prefetch_c(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane,
-                 static_cast<int64_t>(nt) * BNQ + 32 * half);
+      if (g->ksplit <= 1)
+        prefetch_c(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane,
+                   static_cast<int64_t>(nt) * BNQ + 32 * half);
       float acc[128];
 #pragma unroll
       for (int i = 0; i < 128; ++i) acc[i] = 0.f;
@@ -663,8 +699,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(&ctl->accempty[b]);
       }
       if (!ok) break;
-      epilogue(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane,
-               static_cast<int64_t>(nt) * BNQ + 32 * half, acc);
+      if (g->ksplit > 1)
+        store_partial(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane,
+                      static_cast<int64_t>(nt) * BNQ + 32 * half, z, acc);
+      else
+        epilogue(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane,
+                 static_cast<int64_t>(nt) * BNQ + 32 * half, acc);
     }
   }
 

@@ -147,3 +147,93 @@ def test_fused_single_problem_path(opA, opB, layout, monkeypatch):
     got = dC.double().cpu().numpy()
     assert rel_fro(qsynth.components(got, m, layout), qsynth.components(ref, m, layout)) <= TOL
     assert np.all(np.isnan(padding(got, m, layout)))
+
+
+# ---------------------------------------------------------------- K split ---
+def split_shares(m, n, k, sms):
+    """Shares the split-BF16 path splits a single product into (tiles of 128
+    x 64 quaternions, one CTA per SM, >= 64 k-blocks of 32 reals each)."""
+    tiles = -(-m // 128) * -(-n // 64)
+    if tiles >= 8 * sms:
+        return 1
+    num_kb = -(-4 * k // 32)
+
+    def busy(s):
+        return tiles * s / (-(-tiles * s // sms) * sms)
+    shares = range(2, min(256, num_kb // 64) + 1)
+    top = max([busy(1)] + [busy(s) for s in shares])
+    if top < busy(1) + 0.05:
+        return 1
+    return min(s for s in shares if busy(s) >= top - 0.02)
+
+
+SPLIT_SHAPES = [(64, 64, 20000), (37, 29, 8000), (200, 130, 6000), (1, 1, 10000)]
+
+
+@pytest.mark.parametrize("layout", qsynth.LAYOUTS)
+@pytest.mark.parametrize("shape", SPLIT_SHAPES)
+@pytest.mark.parametrize("ops_", [("N", "N"), ("H", "N"), ("T", "C")])
+def test_split_k_parity(ops_, shape, layout):
+    """Few tiles of C, long k: K shares' FP32 products summed in FP64 by a
+    second kernel, then alpha and beta; 2e-6 as unsplit."""
+    m, n, k = shape
+    assert split_shares(m, n, k, torch.cuda.get_device_properties(0).multi_processor_count) > 1
+    check(ops_[0], ops_[1], m, n, k, layout, seed=m + n + k % 991)
+
+
+def test_split_k_small_int_exact():
+    check("N", "H", 37, 29, 8000, "interleaved", seed=8100, kind="int",
+          alpha=np.array([1.0, -2.0, 0.0, 1.0]), beta=np.array([2.0, 0, 1.0, -1.0]))
+
+
+def test_split_k_beta_zero_does_not_read_c():
+    m, n, k = 64, 64, 20000
+    A, B, C = make_case("N", "N", m, n, k, "interleaved", 8200, dtype=np.float32)
+    ref = oracle_full("N", "N", m, n, k, ALPHA, A, B, np.zeros(4), C, "interleaved")
+    C[:, :m] = np.nan
+    got = gpu_run("N", "N", m, n, k, ALPHA, A, B, np.zeros(4), C, "interleaved",
+                  dtype=torch.float32)
+    assert rel_fro(got[:, :m], ref[:, :m]) <= TOL
+
+
+def test_split_k_optional_part_and_speed():
+    """The minimum workspace runs K unsplit, the reported one splits it: both
+    results within 2e-6 of the oracle, and the split run much faster (one
+    tile of C leaves 151 SMs idle unsplit)."""
+    m, n, k = 64, 64, 65536
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ks = split_shares(m, n, k, sms)
+    assert ks > 1
+    L = _abi.lib()
+    full = L.qgemm_workspace_bytes(0, 0, m, n, k, 0, 1)
+    need_min = full - ks * m * n * 16
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(83)
+    A = torch.randn((k, m, 4), dtype=torch.float32, device="cuda", generator=gen)
+    B = torch.randn((n, k, 4), dtype=torch.float32, device="cuda", generator=gen)
+    ws = torch.empty(full, dtype=torch.uint8, device="cuda")
+    one, zero = _abi.q4([1, 0, 0, 0]), _abi.q4([0, 0, 0, 0])
+    stream = torch.cuda.current_stream().cuda_stream
+    outs, times = [], []
+    for wb in (full, need_min):
+        C = torch.zeros((n, m, 4), dtype=torch.float32, device="cuda")
+
+        def call():
+            _abi.check(L.qgemm(0, 0, m, n, k, one, A.data_ptr(), m, 0, B.data_ptr(), k, 0,
+                               zero, C.data_ptr(), m, 0, 0, 1, ws.data_ptr(), wb, stream))
+        call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        call()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        outs.append(C.double().cpu().numpy())
+    print("split %.2f ms, unsplit %.2f ms" % tuple(times))
+    ref = qsynth.empty(m, n, pad=0.0)
+    orc.qgemm("N", "N", m, n, k, np.array([1.0, 0, 0, 0]), A.double().cpu().numpy(),
+              B.double().cpu().numpy(), np.zeros(4), ref)
+    for out in outs:                 # each within the bar of the exact product
+        assert rel_fro(out, ref) <= TOL
+    assert times[0] * 3 < times[1]
