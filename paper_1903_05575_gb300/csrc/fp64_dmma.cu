@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(256)
     const int64_t i = e % m, j = e / m;
     if ((tri == 1 && i < j) || (tri == 2 && i > j)) continue;
     double P[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
     for (int z = 0; z < ksplit; ++z) {
       const double2 *q = reinterpret_cast<const double2 *>(part + z * slab + 4 * e);
       const double2 lo = q[0], hi = q[1];

@@ -1137,7 +1137,7 @@ int sm_count() {
 // quaternions): when C has fewer than 8 waves of tiles, the fewest shares s in
 // [2, 256] whose tiles x s CTAs fill their waves to within 2 % of the best s,
 // with at least 32 k-blocks (256 quaternion k, 4 chunks) per share, if the
-// best beats s = 1 by 5 %.  Plain products only (no triangle, k-range or
+// best beats s = 1 by 5 % and s = 1 keeps at most half of the SMs busy.  Plain products only (no triangle, k-range or
 // turned-around problem).  1: no split.
 int sliced_ksplit(const GemmDesc &d, int sms) {
   if (d.tri || d.krange || d.swap || d.m <= 0 || d.n <= 0 || d.k <= 0) return 1;
@@ -1151,6 +1151,9 @@ int sliced_ksplit(const GemmDesc &d, int sms) {
     const int64_t waves = (ctas + slots - 1) / slots;
     return static_cast<double>(ctas) / static_cast<double>(waves * slots);
   };
+  // under the power cap the BF16 tensor cores gain little from more busy SMs
+  // once half of them work, while the shares cost a write and a re-read
+  if (busy(1) > 0.5) return 1;
   double top = busy(1);
   for (int64_t s = 2; s <= smax; ++s) top = std::max(top, busy(s));
   if (top < busy(1) + 0.05) return 1;

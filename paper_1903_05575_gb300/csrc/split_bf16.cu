@@ -256,6 +256,7 @@ __global__ void __launch_bounds__(256)
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     double P[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
     for (int z = 0; z < ksplit; ++z) {
       const float4 v = *reinterpret_cast<const float4 *>(part + z * slab + 4 * e);
       P[0] += v.x;
@@ -292,7 +293,7 @@ __global__ void __launch_bounds__(256)
 // quaternions): when C has fewer than 8 waves of tiles, the fewest shares s in
 // [2, 256] whose tiles x s CTAs fill their waves to within 2 % of the best s,
 // with at least 64 k-blocks (512 quaternion k) per share, if the best beats
-// s = 1 by 5 %.  Plain products only (no triangle, k-range or turned-around
+// s = 1 by 5 % and s = 1 keeps at most half of the SMs busy.  Plain products only (no triangle, k-range or turned-around
 // problem).  1: no split.
 int split_ksplit(const GemmDesc &d, int sms) {
   if (d.tri || d.krange || d.swap || d.m <= 0 || d.n <= 0 || d.k <= 0) return 1;
@@ -306,6 +307,9 @@ int split_ksplit(const GemmDesc &d, int sms) {
     const int64_t waves = (ctas + slots - 1) / slots;
     return static_cast<double>(ctas) / static_cast<double>(waves * slots);
   };
+  // under the power cap the BF16 tensor cores gain little from more busy SMs
+  // once half of them work, while the shares cost a write and a re-read
+  if (busy(1) > 0.5) return 1;
   double top = busy(1);
   for (int64_t s = 2; s <= smax; ++s) top = std::max(top, busy(s));
   if (top < busy(1) + 0.05) return 1;

@@ -260,6 +260,8 @@ def sliced_split_shares(m, n, k, sms):
 
     def busy(s):
         return tiles * s / (-(-tiles * s // sms) * sms)
+    if busy(1) > 0.5:                # at most half of the SMs busy unsplit
+        return 1
     shares = range(2, min(256, num_kb // 32) + 1)
     top = max([busy(1)] + [busy(s) for s in shares])
     if top < busy(1) + 0.05:
