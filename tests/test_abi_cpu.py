@@ -32,6 +32,54 @@ def test_library_exports_every_declared_symbol():
     assert set(declared_functions()) <= set(_abi.SIGNATURES)
 
 
+def test_plain_c_program_links_and_calls(tmp_path):
+    """The boundary is a C ABI: a C99 program that includes qgemm.h (with
+    -Wall -Wextra -Werror -pedantic), takes the address of every declared
+    entry point, links against the library and calls the ones that need no
+    device (version, workspace sizes, argument checks, quick returns)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    names = declared_functions()
+    lib = _abi.lib_path()
+    src = ["#include <stdio.h>", "#include <stddef.h>", '#include "qgemm.h"', "",
+           "int main(void) {",
+           "  void (*fns[])(void) = {"]
+    src += ["    (void (*)(void))%s," % n for n in names]
+    src += ["  };",
+            "  const double one[4] = {1.0, 0.0, 0.0, 0.0};",
+            "  double c = 0.0;",
+            "  size_t i, live = 0;",
+            "  for (i = 0; i < sizeof fns / sizeof fns[0]; ++i) live += fns[i] != NULL;",
+            "  /* m = 0: returns before any device call */",
+            "  int rc0 = qgemm(QGEMM_OP_N, QGEMM_OP_N, 0, 4, 4, one, NULL, 1, 0, NULL, 4, 0, one,",
+            "                  &c, 1, 0, QGEMM_INTERLEAVED, QGEMM_FP64, NULL, 0, NULL);",
+            "  /* opA = 7: argument 1 invalid */",
+            "  int rc1 = qgemm(7, QGEMM_OP_N, 4, 4, 4, one, NULL, 4, 0, NULL, 4, 0, one,",
+            "                  &c, 4, 0, QGEMM_INTERLEAVED, QGEMM_FP64, NULL, 0, NULL);",
+            "  size_t ws = qgemm_workspace_bytes(QGEMM_OP_N, QGEMM_OP_N, 64, 64, 64,",
+            "                                    QGEMM_INTERLEAVED, QGEMM_FP32_SPLIT_BF16);",
+            '  printf("%zu %d %d %zu %s\\n", live, rc0, rc1, ws, qgemm_version());',
+            "  return 0;",
+            "}"]
+    (tmp_path / "abi.c").write_text("\n".join(src) + "\n")
+    exe = tmp_path / "abi"
+    cmd = [gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+           "-Wno-cast-function-type", "-I", os.path.dirname(HEADER), str(tmp_path / "abi.c"),
+           "-o", str(exe), lib, "-Wl,-rpath," + os.path.dirname(lib)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    live, rc0, rc1, ws, version = out.stdout.split(maxsplit=4)
+    assert int(live) == len(names)
+    assert int(rc0) == 0 and int(rc1) == -1
+    assert int(ws) == _abi.lib().qgemm_workspace_bytes(0, 0, 64, 64, 64, 0, 1) > 0
+    assert version.strip() == _abi.lib().qgemm_version().decode()
+
+
 def _call(**kw):
     a = dict(opA=0, opB=0, m=4, n=4, k=4, alpha=_abi.q4([1, 0, 0, 0]), A=64, lda=4, psA=0,
              B=64, ldb=4, psB=0, beta=_abi.q4([0, 0, 0, 0]), C=64, ldc=4, psC=0, layout=0,
