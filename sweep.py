@@ -3,7 +3,7 @@ N x N products, Sec. 5), printing one JSON line per case:
 
   fp64:  m = n = k in --sizes, every (opA, opB) in --ops, both layouts;
          effective TFLOP/s (32 m n k / t), fraction of the measured DMMA
-         peak, relative error on sampled entries against the FP64 oracle.
+         peak, relative error on sampled entries against an FP64 reference.
   split: m = n = k in --split-sizes, inputs N(0,1) and N(0,1) 2^(u_r + v_c)
          (u, v integers in [-20, 20] per row and column), op N,N; TFLOP/s,
          error, speedup over the FP64 rate at the same size.
@@ -19,9 +19,10 @@ N x N products, Sec. 5), printing one JSON line per case:
 Timing: CUDA events on the launching stream around `reps` calls after
 warm-up; inputs of every case are larger than L2 except the smallest FP64
 sizes, where the call is run `reps` times on the same data (stated in the
-line).  The oracle is only used for the sampled error.
+line).  Errors are on sampled entries against bench.sampled_reference, an
+FP64 numpy computation of those entries.
 
-  python -m paper_1903_05575_gb300.sweep [--sizes 1024,2048,4096] [--ops all|NN]
+  python sweep.py [--sizes 1024,2048,4096] [--ops all|NN]
 """
 import argparse
 import json
@@ -30,6 +31,11 @@ import sys
 import time
 
 import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from bench import sampled_reference  # noqa: E402
 
 
 def _timed(fn, reps, warm=1):
@@ -47,14 +53,10 @@ def _timed(fn, reps, warm=1):
 
 
 def _sampled_error(opA, opB, n, alpha, beta, A, B, C0, C, layout, count=256, seed=1):
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    if root not in sys.path:
-        sys.path.insert(0, root)
     import qsynth
-    from oracle import oracle as orc
     g = np.random.default_rng(seed)
     rows, cols = g.integers(0, n, count), g.integers(0, n, count)
-    ref = orc.qgemm_entries(opA, opB, n, n, n, alpha, A.double().cpu().numpy(),
+    ref = sampled_reference(opA, opB, n, n, n, alpha, A.double().cpu().numpy(),
                             B.double().cpu().numpy(), beta, C0.double().cpu().numpy(), rows, cols,
                             layout=layout)
     got = qsynth.components(C.double().cpu().numpy(), n, layout)[rows, cols]
@@ -65,7 +67,7 @@ def fp64_case(n, opA, opB, layout, peak, reps, precision="fp64"):
     import torch
 
     import qsynth
-    from . import ops
+    from paper_1903_05575_gb300 import ops
     dev = torch.device("cuda", torch.cuda.current_device())
     gen = torch.Generator(device=dev)
     gen.manual_seed(n + 17 * "NTCH".index(opA) + "NTCH".index(opB))
@@ -91,7 +93,7 @@ def split_case(n, kind, fp64_tflops, reps):
     import torch
 
     import qsynth
-    from . import ops
+    from paper_1903_05575_gb300 import ops
     dev = torch.device("cuda", torch.cuda.current_device())
     gen = torch.Generator(device=dev)
     gen.manual_seed(3 * n + (kind == "scaled"))
@@ -123,12 +125,12 @@ def split_case(n, kind, fp64_tflops, reps):
 def trmm_case(n, precision, reps):
     """qtrmm side L, lower, op N, m = n: effective TFLOP/s on the triangular
     product's own work (16 n^3: half the GEMM's), its time relative to the
-    GEMM of the same size and precision, sampled error against the oracle's
-    triangular product."""
+    GEMM of the same size and precision, sampled error against the triangular
+    product computed as a GEMM with tri(A) written out."""
     import torch
 
     import qsynth
-    from . import ops
+    from paper_1903_05575_gb300 import ops
     dev = torch.device("cuda", torch.cuda.current_device())
     dt = torch.float32 if precision == "split_bf16" else torch.float64
     gen = torch.Generator(device=dev)
@@ -143,16 +145,12 @@ def trmm_case(n, precision, reps):
                 reps)
     ops.qtrmm("L", "L", "N", "N", n, n, al, A, B, C, precision=p)
     torch.cuda.synchronize()
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    if root not in sys.path:
-        sys.path.insert(0, root)
-    from oracle import oracle as orc
     g = np.random.default_rng(4)
     rows, cols = g.integers(0, n, 128), g.integers(0, n, 128)
     Ah = A.double().cpu().numpy().copy()
     idx = np.arange(n)
     Ah[idx[:, None] > idx[None, :]] = 0.0  # stored (column, row): keep row >= column
-    ref = orc.qgemm_entries("N", "N", n, n, n, al, Ah, B.double().cpu().numpy(), np.zeros(4),
+    ref = sampled_reference("N", "N", n, n, n, al, Ah, B.double().cpu().numpy(), np.zeros(4),
                             np.zeros_like(Ah), rows, cols)
     got = qsynth.components(C.double().cpu().numpy(), n, "interleaved")[rows, cols]
     err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
@@ -166,7 +164,7 @@ def mixed_case(n, precision, types, reps):
     mixed product and of the quaternion product on the same precision."""
     import torch
 
-    from . import ops
+    from paper_1903_05575_gb300 import ops
     dev = torch.device("cuda", torch.cuda.current_device())
     dt = torch.float32 if precision == "split_bf16" else torch.float64
     width = {"H": 4, "C": 2, "R": 1}
@@ -205,7 +203,7 @@ def complex_comparison(n, reps, qgemm_ms=None):
     dms = _timed(lambda: torch.matmul(R1, R2, out=R3), reps)
     del R1, R2, R3
     if qgemm_ms is None:
-        from . import ops
+        from paper_1903_05575_gb300 import ops
         A = torch.randn((n, n, 4), dtype=torch.float64, device=dev, generator=gen)
         B = torch.randn((n, n, 4), dtype=torch.float64, device=dev, generator=gen)
         C = torch.empty((n, n, 4), dtype=torch.float64, device=dev)
@@ -225,11 +223,11 @@ def splitk_case(m, n, k, peak, reps):
     """FP64 product with a small C and a long k, run with the workspace that
     lets it split K and without one (unsplit); N(0,1) data, op N,N,
     interleaved, unit-quaternion alpha and beta; error of the split result on
-    sampled entries against the oracle."""
+    sampled entries against an FP64 reference."""
     import torch
 
     import qsynth
-    from . import _abi, ops
+    from paper_1903_05575_gb300 import _abi, ops
     dev = torch.device("cuda", torch.cuda.current_device())
     gen = torch.Generator(device=dev)
     gen.manual_seed(m + 3 * n + k)
@@ -252,13 +250,9 @@ def splitk_case(m, n, k, peak, reps):
     C.copy_(C0)
     call(ws.data_ptr(), need)
     torch.cuda.synchronize()
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    if root not in sys.path:
-        sys.path.insert(0, root)
-    from oracle import oracle as orc
     g = np.random.default_rng(3)
     rows, cols = g.integers(0, m, 128), g.integers(0, n, 128)
-    ref = orc.qgemm_entries("N", "N", m, n, k, alpha, A.cpu().numpy(), B.cpu().numpy(), beta,
+    ref = sampled_reference("N", "N", m, n, k, alpha, A.cpu().numpy(), B.cpu().numpy(), beta,
                             C0.cpu().numpy(), rows, cols)
     got = qsynth.components(C.cpu().numpy(), m, "interleaved")[rows, cols]
     err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
@@ -286,7 +280,7 @@ def main():
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--compare", default="", help="sizes for the cuBLAS ZGEMM/DGEMM comparison")
     a = ap.parse_args()
-    from . import ops
+    from paper_1903_05575_gb300 import ops
     peak = ops.probe_peak(0, 0.4)
     pairs = ([x + y for x in "NTCH" for y in "NTCH"] if a.ops == "all" else a.ops.split(","))
     fp64_rate = {}
