@@ -628,7 +628,7 @@ int launch_fused(const qgemm_grouped_plan *plan, cudaStream_t s) {
 }
 
 // The fused path is opt-in (QGEMM_GROUPED_FUSED=1): measured on GB300 its two
-// converter warps limit it below the pre-pass path (config-4 batch 26.7 vs
+// converter warps limit it below the pre-pass path (4096-problem batch 26.7 vs
 // 47.9 TFLOP/s), and more converter warps do not fit the register budget.
 bool fused_enabled() {
   const char *e = std::getenv("QGEMM_GROUPED_FUSED");

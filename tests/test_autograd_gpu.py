@@ -129,7 +129,7 @@ def test_backward_accumulate_and_skip():
     assert rel_fro(dW2.cpu().numpy(), refW2) <= 1e-12
 
 
-def test_config5_full_size_split():
+def test_linear_layer_8192x1024x1024_split():
     """X 8192 x 1024, W 1024 x 1024 (W ~ N(0, 1/4096)), FP32 split path:
     forward Y and backward dX, dW for a seeded dY, sampled against the oracle."""
     mb, k, n = 8192, 1024, 1024
@@ -152,5 +152,5 @@ def test_config5_full_size_split():
                                 rows, cols)
         G = qsynth.components(got.double().cpu().numpy(), M, "interleaved")[rows, cols]
         err = rel_fro(G, ref)
-        print("config5 %s%s rel err %.3e" % (opA, opB, err))
+        print("linear layer %s%s rel err %.3e" % (opA, opB, err))
         assert err <= 2e-6

@@ -34,7 +34,7 @@ def check(opA, opB, m, n, k, layout, seed, kind="normal", alpha=ALPHA, beta=BETA
     assert np.all(np.isnan(padding(got, m, layout))), "padding rows written"
 
 
-def test_config1_parity():
+def test_fp64_256_cubed_parity():
     """FP64, op N,N, m=n=k=256, alpha=1, beta=0, N(0,1), interleaved."""
     m = n = k = 256
     A = qsynth.normal(m, k, 1903)
@@ -44,7 +44,7 @@ def test_config1_parity():
     ref = oracle_full("N", "N", m, n, k, one, A, B, zero, C, "interleaved")
     got = gpu_run("N", "N", m, n, k, one, A, B, zero, C, "interleaved")
     err = rel_fro(got, ref)
-    print("config1 rel_fro = %.3e" % err)
+    print("256^3 rel_fro = %.3e" % err)
     assert err <= TOL
 
 

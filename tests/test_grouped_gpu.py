@@ -116,7 +116,7 @@ def test_invalid_problem_reports_index_and_argument():
     assert rc == -(1000 * 2 + 11)
 
 
-def test_config4_fp64_batch_sampled():
+def test_batch_4096_problems_fp64_sampled():
     """4096 problems, m, n, k iid uniform in [8, 256], ops iid in {N, H}."""
     probs = qsynth.grouped_problems(4096, 1907)
     specs = [(p["opA"], p["opB"], p["m"], p["n"], p["k"]) for p in probs]
@@ -125,7 +125,7 @@ def test_config4_fp64_batch_sampled():
     b.launch()
     torch.cuda.synchronize()
     worst = check_batch(host, dev, "interleaved", 1e-12, full=False)
-    print("config4 fp64 worst sampled rel err %.3e" % worst)
+    print("4096-problem batch fp64 worst sampled rel err %.3e" % worst)
 
 
 def test_graph_capture_and_replay():
@@ -169,7 +169,7 @@ def test_mixed_batch_split(layout):
     assert _abi.lib().qgemm_get_last_device_error() == 0
 
 
-def test_config4_split_batch_sampled_and_graph():
+def test_batch_4096_problems_split_sampled_and_graph():
     probs = qsynth.grouped_problems(4096, 1908)
     specs = [(p["opA"], p["opB"], p["m"], p["n"], p["k"]) for p in probs]
     host, dev = make_batch(specs, "interleaved", dtype=np.float32, seed=800, pad=0)
@@ -188,7 +188,7 @@ def test_config4_split_batch_sampled_and_graph():
     gr.replay()
     torch.cuda.synchronize()
     worst = check_batch(host, dev, "interleaved", 2e-6, full=False)
-    print("config4 split worst sampled rel err %.3e" % worst)
+    print("4096-problem batch split worst sampled rel err %.3e" % worst)
 
 
 @pytest.mark.parametrize("fused", ["1", "0"])
@@ -305,7 +305,7 @@ def test_sliced_graph_replay():
         check_batch(host, dev, "interleaved", 1e-12)
 
 
-def test_config4_sliced_batch_sampled():
+def test_batch_4096_problems_sliced_sampled():
     """4096 problems, m, n, k iid uniform in [8, 256], ops iid in {N, H},
     FP64 data on the digit-sliced path."""
     probs = qsynth.grouped_problems(4096, 1907)
@@ -315,5 +315,5 @@ def test_config4_sliced_batch_sampled():
     b.launch()
     torch.cuda.synchronize()
     worst = check_batch(host, dev, "interleaved", 1e-12, full=False)
-    print("config4 sliced worst sampled rel err %.3e" % worst)
+    print("4096-problem batch sliced worst sampled rel err %.3e" % worst)
     assert _abi.lib().qgemm_get_last_device_error() == 0
