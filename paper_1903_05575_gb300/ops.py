@@ -64,7 +64,13 @@ def _stream_handle(stream):
 
 def qgemm(opA, opB, m, n, k, alpha, A, B, beta, C, layout="interleaved", ws=None,
           stream=None, precision=None):
-    """C <- alpha op(A) op(B) + beta C on the GPU (C is updated in place)."""
+    """C <- alpha op(A) op(B) + beta C on the GPU (C is updated in place).
+
+    ws: a uint8 device tensor, or None for the module's cached workspace of
+    the size qgemm_workspace_bytes reports.  That size includes the optional
+    part that lets a product with a small C and a long k split K across CTAs
+    (the only workspace the FP64 path uses); a smaller ws runs K unsplit, or
+    fails with the ABI's -20 below the tensor-core paths' minimum."""
     prec = precision_of(C.dtype, precision)
     if A.dtype != C.dtype or B.dtype != C.dtype:
         raise TypeError("A, B and C must share a dtype")
