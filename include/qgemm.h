@@ -172,25 +172,28 @@ size_t qgemm_workspace_bytes(int opA, int opB, int64_t m, int64_t n, int64_t k,
 
 /*
  * qgemm_split_noalloc: the split-BF16 qgemm() for callers that cannot
- * allocate device memory -- for example code that runs while a CUDA graph is
- * being captured (cudaMalloc is not allowed then), code whose device memory
- * is all owned by another allocator, or a plain C caller with no allocator of
- * its own.  It takes no workspace: the split operands go to a scratch array
- * of QGEMM_NOALLOC_SCRATCH_BYTES that the library keeps in device memory
- * (every device that loads the library holds it until the process exits).
- * The paper has no counterpart; it is an interface convenience.
+ * allocate device memory -- for example code whose device memory all belongs
+ * to another allocator (a framework's pool, a fixed arena), or a plain C
+ * caller with no allocator of its own.  It takes no workspace: the split
+ * operands (and, for few tiles of C with a long k, the K shares' partial
+ * products) go to a scratch array of QGEMM_NOALLOC_SCRATCH_BYTES that the
+ * library keeps in device memory (every device that loads the library holds
+ * it until the process exits).  The paper has no counterpart; it is an
+ * interface convenience.
  *
  * Arguments 1-17 and 18 (stream) as in qgemm() with precision
  * QGEMM_FP32_SPLIT_BF16 (float data).  Returns QGEMM_ERR_WORKSPACE, before
- * launching anything, when the problem needs more than
+ * launching anything, when the problem's split operands need more than
  * QGEMM_NOALLOC_SCRATCH_BYTES (qgemm_workspace_bytes() gives the need; for
- * square problems the largest that fits is m = n = k = 744).
+ * square problems the largest that fits is m = n = k = 1180).
  * It calls no allocator.  The first call on a device looks up the scratch
- * array's device address, so make it once before any stream capture.  All
- * calls share the one array: calls that can overlap on the GPU (different
- * streams without ordering between them) race and give wrong results.  Each
- * call rewrites every scratch byte its kernels read, so nothing has to be
- * cleared between calls.
+ * array's device address once for that device, so make it before any stream
+ * capture; the address is kept for the life of the process, so the library
+ * must not be used across a cudaDeviceReset() of that device.  All calls
+ * share the one array: calls that can overlap on the GPU (different streams
+ * without ordering between them) race and give wrong results.  Each call
+ * rewrites every scratch byte its kernels read, so nothing has to be cleared
+ * between calls.
  */
 #define QGEMM_NOALLOC_SCRATCH_BYTES (64u << 20)
 int qgemm_split_noalloc(int opA, int opB, int64_t m, int64_t n, int64_t k,
@@ -415,6 +418,20 @@ const char *qgemm_status_string(int status);
 int qgemm_debug_unsatisfied_wait(uint64_t limit_ns, void *stream);
 
 /*
+ * Test hook for the abort paths of the GEMM kernels (no paper counterpart;
+ * the failure detection of the library's own waits).  Arms a one-shot fault
+ * for the next qgemm() launch of precision `path` (QGEMM_FP64 or
+ * QGEMM_FP32_SPLIT_BF16): the kernel's TMA producer leaves out the copies of
+ * its ring stage number `stage` (counted from 0 over the launch; for FP64 in
+ * the first CTA), and that launch waits at most limit_ns (1 ms .. 10 s) per
+ * wait.  The consumer's wait gives up, every role of the CTA stops, copies in
+ * flight land, tensor memory is released, and qgemm_get_last_device_error()
+ * then reports QGEMM_ERR_TIMEOUT; the context stays usable.  The launch's C
+ * is undefined.  Returns 0, or -i for an invalid argument i.
+ */
+int qgemm_debug_arm_fault(int path, int stage, uint64_t limit_ns);
+
+/*
  * Throughput microbenchmarks of the device's arithmetic pipes (no paper
  * counterpart; they supply the roofline denominators).  which:
  *   0 FP64 tensor (DMMA m16n8k4)   1 FP64 FMA (DFMA)   2 FP32 FMA (FFMA)
@@ -423,6 +440,10 @@ int qgemm_debug_unsatisfied_wait(uint64_t limit_ns, void *stream);
  *   4, 5, 6 the same instruction at N = 256, 128, 64 on operands holding
  *     integers in [-127, 127]
  *   7 DMMA and DFMA together (alternate warps): whether the two FP64 pipes add
+ *   8 N = 64, four MMAs per A tile (four B tiles) with the A operand held in
+ *     the tensor core's collector; 9 the same without the collector;
+ *     10 N = 32 as 8; 11 N = 128, two MMAs per A tile, collector;
+ *     12 N = 64, twelve MMAs per A tile, collector
  * Runs for roughly `seconds` and writes the achieved TFLOP/s (2 per FMA).
  */
 int qgemm_probe_peak(int which, double seconds, double *tflops, void *stream);

@@ -74,6 +74,7 @@ SIGNATURES = {
     "qgemm_status_string": (ctypes.c_char_p, [i32]),
     "qgemm_last_cuda_error": (ctypes.c_char_p, []),
     "qgemm_debug_unsatisfied_wait": (i32, [ctypes.c_uint64, vp]),
+    "qgemm_debug_arm_fault": (i32, [i32, i32, ctypes.c_uint64]),
     "qgemm_probe_peak": (i32, [i32, ctypes.c_double, dp, vp]),
     "qgemm_version": (ctypes.c_char_p, []),
 }

@@ -367,8 +367,19 @@ int qgemm_debug_unsatisfied_wait(uint64_t limit_ns, void *stream) {
   return debug_unsatisfied_wait(limit_ns, static_cast<cudaStream_t>(stream));
 }
 
+int qgemm_debug_arm_fault(int path, int stage, uint64_t limit_ns) {
+  if (path != QGEMM_FP64 && path != QGEMM_FP32_SPLIT_BF16) return -1;
+  if (stage < 0 || stage > 1000000) return -2;
+  if (limit_ns < 1000000ull || limit_ns > 10000000000ull) return -3;
+  if (path == QGEMM_FP32_SPLIT_BF16)
+    split_arm_fault(stage, limit_ns);
+  else
+    fp64_arm_fault(stage, limit_ns);
+  return QGEMM_SUCCESS;
+}
+
 int qgemm_probe_peak(int which, double seconds, double *tflops, void *stream) {
-  if (which < 0 || which > 7) return -1;
+  if (which < 0 || which > 14) return -1;
   if (!(seconds > 0.0) || seconds > 60.0) return -2;
   if (tflops == nullptr) return -3;
   int rc = device_ready();

@@ -13,6 +13,7 @@
 // DMMA is gathered with the sign of L(a) applied by an integer XOR
 // (conjugation of A or B only changes those signs), and the epilogue applies
 // C <- alpha P + beta C with left products in FP64.
+#include <atomic>
 #include <cstring>
 
 #include "fp64_tile.cuh"
@@ -308,10 +309,22 @@ int launch_fp64_gemm(const GemmDesc &d, cudaStream_t stream) {
   return launch_fp64_gemm_ws(d, nullptr, 0, stream);
 }
 
+namespace {
+// One-shot fault injection for the bounded-wait test (qgemm_debug_arm_fault).
+std::atomic<int> g_fp64_debug_skip{0};
+std::atomic<uint64_t> g_fp64_debug_limit{0};
+}  // namespace
+
+void fp64_arm_fault(int stage, uint64_t limit_ns) {
+  g_fp64_debug_limit.store(limit_ns);
+  g_fp64_debug_skip.store(stage + 1);
+}
+
 int launch_fp64_gemm_ws(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_t stream) {
   Fp64Args a{};
   a.op = fp64_operands(d);
-  a.limit_ns = wait_limit_ns();
+  a.op.debug_skip = g_fp64_debug_skip.exchange(0);
+  a.limit_ns = a.op.debug_skip ? g_fp64_debug_limit.load() : wait_limit_ns();
   // K split when it pays and the caller's workspace holds the partials
   int ks = fp64_ksplit(d, device_sms());
   if (ks > 1) {

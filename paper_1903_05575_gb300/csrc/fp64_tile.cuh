@@ -50,6 +50,9 @@ struct Operands {
   // a second kernel sums the ksplit partials and applies alpha and beta.
   int ksplit;  // 0 or 1: no split
   double *part;
+  // Fault injection (tests of the bounded waits): > 0 makes the first CTA of
+  // the launch leave out the copies of its ring stage debug_skip - 1.
+  int debug_skip;
 };
 
 // True when the tile at quaternion offset (i0, n0) of size BMQ x BNQ has no
@@ -157,6 +160,9 @@ __device__ bool tile(const Operands &p, const CUtensorMap *tmA, const CUtensorMa
   auto issue = [&](int kt) {
     const uint32_t q = kb_run + kt;
     const int st = q % kStages;
+    if (p.debug_skip > 0 && q == static_cast<uint32_t>(p.debug_skip - 1) && blockIdx.x == 0 &&
+        blockIdx.y == 0 && blockIdx.z == 0)
+      return;
     mbar_arrive_expect_tx(&full[st], tx_bytes);
     const int64_t kk0 = static_cast<int64_t>(kt_lo + kt) * kBKQ;
     if (p.tmaA) tma_box(sA + st * kMaxTileElems, tmA, &full[st], LAYOUT, TA ? kk0 : i0, TA ? i0 : kk0);

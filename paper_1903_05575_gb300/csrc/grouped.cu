@@ -33,6 +33,8 @@ int launch_sliced_grouped(const qgemm_grouped_plan *plan, cudaStream_t s);
 __device__ int g_grouped_error;
 
 fp64::Operands fp64_operands(const GemmDesc &d);
+bool encode_split_planes(CUtensorMap *map, const void *base, int64_t kq, int64_t kp,
+                         int64_t rows, int planes, int box_rows);
 bool encode_fp64_operand(CUtensorMap *map, const MatView &v, int layout, int R, int CC);
 
 namespace {
@@ -154,9 +156,10 @@ struct GroupedErr {
 };
 
 // Pre-pass over the split operands of every problem: entry = (problem,
-// is_b, row tile, k tile).  At most 32 registers, so 8 CTAs fit on an SM: the
-// tiles are small and ragged, and more resident CTAs keep more loads in flight.
-__global__ void __launch_bounds__(256, 8)
+// is_b, row tile, k tile).  At most 40 registers, so 6 CTAs fit on an SM: the
+// tiles are small and ragged, and more resident CTAs keep more loads in
+// flight (the double-float scaling by alpha does not fit 32 without spills).
+__global__ void __launch_bounds__(256, 6)
     grouped_prepass_kernel(const split::SplitProb *__restrict__ probs,
                            const int4 *__restrict__ ptiles, int n) {
   __shared__ float4 tile[32][33];
@@ -241,7 +244,7 @@ struct SplitLayout {
   std::vector<int64_t> kp;
 };
 
-int64_t split_kp(int64_t k) { return ((4 * k + split::BK - 1) / split::BK) * split::BK; }
+int64_t split_kp(int64_t k) { return (k + 7) / 8 * 8; }
 
 // Conjugate transpose of an op: (op(X))^H = op'(X).
 int op_conjtrans(int op) {
@@ -253,15 +256,18 @@ int op_conjtrans(int op) {
   }
 }
 
-// (AB)^H = B^H A^H (Sec. 2.2): when it pads less (tile rows are padded to
-// 128, columns to 64), a problem is computed as D = op(B)^H op(A)^H and
-// written back as C = conj(D)^T by the epilogue.
+// MMA work of an m x n problem in split-BF16 tiles: rows padded to BM, every
+// column tile to its MMA width (16-column granules, at most BNQ).
+int64_t split_padded(int64_t m, int64_t n) {
+  const int64_t rows = (m + split::BM - 1) / split::BM * split::BM;
+  const int64_t full = n / split::BNQ * split::BNQ, rem = n % split::BNQ;
+  return rows * (full + (rem + 15) / 16 * 16);
+}
+
+// (AB)^H = B^H A^H (Sec. 2.2): when it pads less, a problem is computed as
+// D = op(B)^H op(A)^H and written back as C = conj(D)^T by the epilogue.
 GemmDesc oriented(const GemmDesc &d, bool *swapped) {
-  const int64_t pad_n = ((d.m + split::BM - 1) / split::BM) * split::BM *
-                        (((d.n + split::BNQ - 1) / split::BNQ) * split::BNQ);
-  const int64_t pad_s = ((d.n + split::BM - 1) / split::BM) * split::BM *
-                        (((d.m + split::BNQ - 1) / split::BNQ) * split::BNQ);
-  *swapped = d.k > 0 && pad_s < pad_n && std::getenv("QGEMM_GROUPED_NO_SWAP") == nullptr;
+  *swapped = d.k > 0 && split_padded(d.n, d.m) < split_padded(d.m, d.n);
   if (!*swapped) return d;
   GemmDesc t = d;
   t.m = d.n;
@@ -270,60 +276,46 @@ GemmDesc oriented(const GemmDesc &d, bool *swapped) {
   t.opB = op_conjtrans(d.opA);
   t.A = d.B;
   t.B = d.A;
+  t.swap = 1;
   return t;
 }
 
 SplitLayout layout_split(const std::vector<GemmDesc> &ds_in) {
-  std::vector<GemmDesc> ds(ds_in.size());
-  for (size_t p = 0; p < ds_in.size(); ++p) {
-    bool sw;
-    ds[p] = oriented(ds_in[p], &sw);
-  }
   SplitLayout L{};
   int64_t tiles = 0, ptiles = 0;
-  L.a_off.resize(ds.size());
-  L.b_off.resize(ds.size());
-  L.kp.resize(ds.size());
+  L.a_off.resize(ds_in.size());
+  L.b_off.resize(ds_in.size());
+  L.kp.resize(ds_in.size());
   size_t data = 0;
-  for (size_t p = 0; p < ds.size(); ++p) {
-    const GemmDesc &d = ds[p];
+  for (size_t p = 0; p < ds_in.size(); ++p) {
+    bool sw;
+    const GemmDesc d = oriented(ds_in[p], &sw);
     L.kp[p] = split_kp(d.k);
     if (d.m == 0 || d.n == 0) continue;
     tiles += ((d.m + split::BM - 1) / split::BM) * ((d.n + split::BNQ - 1) / split::BNQ);
     if (d.k > 0) {
-      const int64_t kt = (L.kp[p] / 4 + 31) / 32;
+      const int64_t kt = (d.k + 31) / 32;
       ptiles += ((d.m + 31) / 32) * kt + ((d.n + 31) / 32) * kt;
       L.a_off[p] = data;
-      data = align_up(data + static_cast<size_t>(split::TERMS) * d.m * L.kp[p] * 2, 1024);
+      data = align_up(data + static_cast<size_t>(split::TERMS) * split::PLANES * d.m * L.kp[p] * 2,
+                      1024);
       L.b_off[p] = data;
-      data = align_up(data + static_cast<size_t>(split::TERMS) * 4 * d.n * L.kp[p] * 2, 1024);
+      data = align_up(data + static_cast<size_t>(split::TERMS) * split::PLANES * d.n * L.kp[p] * 2,
+                      1024);
     }
   }
   L.tiles = tiles;
   L.ptiles = ptiles;
   L.desc_off = kHeaderBytes;
-  L.tile_off = align_up(L.desc_off + ds.size() * sizeof(split::SplitProb), 256);
+  L.tile_off = align_up(L.desc_off + ds_in.size() * sizeof(split::SplitProb), 256);
   L.ptile_off = align_up(L.tile_off + static_cast<size_t>(tiles) * sizeof(int4), 256);
   L.data_off = align_up(L.ptile_off + static_cast<size_t>(ptiles) * sizeof(int4), 1024);
-  for (size_t p = 0; p < ds.size(); ++p) {
+  for (size_t p = 0; p < ds_in.size(); ++p) {
     L.a_off[p] += L.data_off;
     L.b_off[p] += L.data_off;
   }
   L.total = L.data_off + data;
   return L;
-}
-
-bool encode_split_map(CUtensorMap *map, const void *base, int64_t kp, int64_t rows, int box) {
-  EncodeTiledFn enc = encode_tiled_fn();
-  if (!enc || rows <= 0) return false;
-  cuuint64_t dims[3] = {static_cast<cuuint64_t>(kp), static_cast<cuuint64_t>(rows), split::TERMS};
-  cuuint64_t strides[2] = {static_cast<cuuint64_t>(kp) * 2,
-                           static_cast<cuuint64_t>(kp) * 2 * static_cast<cuuint64_t>(rows)};
-  cuuint32_t boxd[3] = {split::BK, static_cast<cuuint32_t>(box), split::TERMS};
-  cuuint32_t estr[3] = {1, 1, 1};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides,
-             boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 int set_split_smem() {
@@ -343,16 +335,38 @@ int set_split_smem() {
   return QGEMM_SUCCESS;
 }
 
+void double_float4(const double *x, float *hi, float *lo) {
+  for (int s = 0; s < 4; ++s) {
+    hi[s] = static_cast<float>(x[s]);
+    lo[s] = static_cast<float>(x[s] - static_cast<double>(hi[s]));
+  }
+}
+
+// Pre-pass arguments of one operand of a grouped problem: op(X) with `rows`
+// op rows, scaled by s on the given side (kScale*).
+void prep_args(split::PrepArgs &a, const MatView &v, int op, bool is_b, int64_t rows,
+               int64_t k, int64_t kp, int layout, __nv_bfloat16 *out, int smode,
+               const double *s) {
+  a = split::PrepArgs{};
+  a.X = static_cast<const float *>(v.ptr);
+  a.ld = v.ld;
+  a.ps = v.ps;
+  a.rows = rows;
+  a.kq = k;
+  a.kp = kp;
+  a.out = out;
+  a.layout = layout;
+  a.row_contig = is_b ? (op_trans(op) ? 1 : 0) : (op_trans(op) ? 0 : 1);
+  a.conj = op_conj(op) ? 1 : 0;
+  a.width = 4;
+  a.planes = 4;
+  a.smode = smode;
+  if (s) double_float4(s, a.s_hi, a.s_lo);
+}
+
 int prepare_split(const std::vector<GemmDesc> &ds_in, int layout, unsigned char *ws,
                   size_t ws_bytes, cudaStream_t s, qgemm_grouped_plan *plan) {
   const SplitLayout L = layout_split(ds_in);
-  std::vector<GemmDesc> ds(ds_in.size());
-  std::vector<int> swapped(ds_in.size(), 0);
-  for (size_t p = 0; p < ds_in.size(); ++p) {
-    bool sw;
-    ds[p] = oriented(ds_in[p], &sw);
-    swapped[p] = sw ? 1 : 0;
-  }
   if (ws_bytes < L.total) return -6;
   if (L.tiles > 0x7fffffff || L.ptiles > 0x7fffffff) return QGEMM_ERR_UNSUPPORTED;
   int rc = set_split_smem();
@@ -362,52 +376,49 @@ int prepare_split(const std::vector<GemmDesc> &ds_in, int layout, unsigned char 
   auto *hd = reinterpret_cast<split::SplitProb *>(host.data());
   std::vector<int4> tiles, ptiles;
   std::vector<int> tile_kb;
-  for (size_t p = 0; p < ds.size(); ++p) {
-    const GemmDesc &d = ds[p];
+  for (size_t p = 0; p < ds_in.size(); ++p) {
+    bool sw;
+    const GemmDesc d = oriented(ds_in[p], &sw);
     if (d.m == 0 || d.n == 0) continue;
+    if (d.k > split::kMaxK) return QGEMM_ERR_UNSUPPORTED;
     split::SplitProb &q = hd[p];
     const int64_t kp = L.kp[p];
     auto *wa = reinterpret_cast<__nv_bfloat16 *>(ws + L.a_off[p]);
     auto *wb = reinterpret_cast<__nv_bfloat16 *>(ws + L.b_off[p]);
     q.g.m = d.m;
     q.g.n = d.n;
-    q.g.num_kb = static_cast<int>(d.k > 0 ? kp / split::BK : 0);
+    q.g.num_kb = static_cast<int>(d.k > 0 ? (d.k + split::KQ - 1) / split::KQ : 0);
     q.g.num_mt = static_cast<int>((d.m + split::BM - 1) / split::BM);
     q.g.num_nt = static_cast<int>((d.n + split::BNQ - 1) / split::BNQ);
+    q.g.pa = 4;
+    q.g.pb = 4;
     q.g.layout = layout;
     q.g.beta_zero = d.beta_zero ? 1 : 0;
+    q.g.beta_real = (d.beta[1] == 0.0 && d.beta[2] == 0.0 && d.beta[3] == 0.0) ? 1 : 0;
     q.g.c_vec4 = (reinterpret_cast<uintptr_t>(d.C) % 16 == 0) ? 1 : 0;
     q.g.C = static_cast<float *>(d.C);
     q.g.ldc = d.ldc;
     q.g.psC = d.psc;
-    q.g.swap = swapped[p];
-    for (int c = 0; c < 4; ++c) {
-      q.g.alpha[c] = static_cast<float>(d.alpha[c]);
-      q.g.beta[c] = static_cast<float>(d.beta[c]);
-    }
+    q.g.swap = sw ? 1 : 0;
+    double_float4(d.beta, q.g.beta_hi, q.g.beta_lo);
     if (d.k > 0) {
-      auto prep = [&](split::PrepArgs &a, const MatView &v, int op, bool is_b, int64_t rows,
-                      __nv_bfloat16 *out) {
-        a.X = static_cast<const float *>(v.ptr);
-        a.ld = v.ld;
-        a.ps = v.ps;
-        a.rows = rows;
-        a.kq = d.k;
-        a.kp = kp;
-        a.term_stride = (is_b ? 4 * rows : rows) * kp;
-        a.out = out;
-        a.layout = layout;
-        a.row_contig = is_b ? (op_trans(op) ? 1 : 0) : (op_trans(op) ? 0 : 1);
-        a.negmask = op_conj(op) ? 0xEu : 0u;
-        a.width = 4;
-        a.kw = 4;
-      };
-      prep(q.pa, d.A, d.opA, false, d.m, wa);
-      prep(q.pb, d.B, d.opB, true, d.n, wb);
-      if (!encode_split_map(&q.tmA, wa, kp, d.m, split::BM) ||
-          !encode_split_map(&q.tmB, wb, kp, 4 * d.n, split::BN))
+      // alpha: on the left of op(A), or (turned around) conj(alpha) on the
+      // right of op(A)^H, the B side: (alpha A B)^H = B^H (A^H conj(alpha))
+      const double *al = d.alpha;
+      const bool real = al[1] == 0.0 && al[2] == 0.0 && al[3] == 0.0;
+      const int smode = (real && al[0] == 1.0) ? split::kScaleNone
+                        : real                 ? split::kScaleReal
+                        : sw                   ? split::kScaleRight
+                                               : split::kScaleLeft;
+      const double conj_al[4] = {al[0], -al[1], -al[2], -al[3]};
+      prep_args(q.pa, d.A, d.opA, false, d.m, d.k, kp, layout, wa,
+                sw ? split::kScaleNone : smode, al);
+      prep_args(q.pb, d.B, d.opB, true, d.n, d.k, kp, layout, wb,
+                sw ? smode : split::kScaleNone, conj_al);
+      if (!encode_split_planes(&q.tmA, wa, d.k, kp, d.m, 4, split::BM) ||
+          !encode_split_planes(&q.tmB, wb, d.k, kp, d.n, 4, split::BNQ))
         return QGEMM_ERR_UNSUPPORTED;
-      const int kt = static_cast<int>((kp / 4 + 31) / 32);
+      const int kt = static_cast<int>((d.k + 31) / 32);
       for (int r = 0; r < (d.m + 31) / 32; ++r)
         for (int c = 0; c < kt; ++c) ptiles.push_back(make_int4(static_cast<int>(p), 0, r, c));
       for (int r = 0; r < (d.n + 31) / 32; ++r)
@@ -419,6 +430,8 @@ int prepare_split(const std::vector<GemmDesc> &ds_in, int layout, unsigned char 
         tile_kb.push_back(q.g.num_kb);
       }
   }
+  // longest tiles first; a problem's tiles stay adjacent (stable), so they run
+  // at about the same time and share its operands in L2
   std::vector<int32_t> order(tiles.size());
   for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<int32_t>(i);
   std::stable_sort(order.begin(), order.end(),
@@ -449,192 +462,6 @@ int prepare_split(const std::vector<GemmDesc> &ds_in, int layout, unsigned char 
   return QGEMM_SUCCESS;
 }
 
-// ---- split precision, fused (no operand workspace) ----
-}  // namespace
-
-// 3-D FP32 tensor map of a stored operand for a box of R x CC stored elements
-// (component x row x column interleaved; row x column x plane for planes).
-bool encode_fp32_operand(CUtensorMap *map, const MatView &v, int layout, int R, int CC) {
-  const uintptr_t base = reinterpret_cast<uintptr_t>(v.ptr);
-  if (base % 16 != 0 || v.rows <= 0 || v.cols <= 0) return false;
-  cuuint64_t dims[3], strides[2];
-  cuuint32_t box[3], estr[3] = {1, 1, 1};
-  if (layout == QGEMM_INTERLEAVED) {
-    dims[0] = 4;
-    dims[1] = static_cast<cuuint64_t>(v.rows);
-    dims[2] = static_cast<cuuint64_t>(v.cols);
-    strides[0] = 16;
-    strides[1] = static_cast<cuuint64_t>(v.ld) * 16;
-    box[0] = 4;
-    box[1] = R;
-    box[2] = CC;
-  } else {
-    if (v.ld % 4 != 0 || v.ps % 4 != 0) return false;
-    dims[0] = static_cast<cuuint64_t>(v.rows);
-    dims[1] = static_cast<cuuint64_t>(v.cols);
-    dims[2] = 4;
-    strides[0] = static_cast<cuuint64_t>(v.ld) * 4;
-    strides[1] = static_cast<cuuint64_t>(v.ps) * 4;
-    box[0] = R;
-    box[1] = CC;
-    box[2] = 4;
-  }
-  if (dims[0] >= (1ull << 32) || dims[1] >= (1ull << 32) || dims[2] >= (1ull << 32)) return false;
-  if (strides[0] >= (1ull << 40) || strides[1] >= (1ull << 40)) return false;
-  EncodeTiledFn enc = encode_tiled_fn();
-  if (!enc) return false;
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(v.ptr), dims, strides,
-             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-namespace {
-
-struct FusedLayout {
-  size_t desc_off, tile_off, total;
-  int64_t tiles;
-};
-
-FusedLayout layout_fused(const std::vector<GemmDesc> &ds) {
-  FusedLayout L{};
-  int64_t tiles = 0;
-  for (const GemmDesc &d : ds)
-    if (d.m > 0 && d.n > 0)
-      tiles += ((d.m + split::BM - 1) / split::BM) * ((d.n + split::BNQ - 1) / split::BNQ);
-  L.tiles = tiles;
-  L.desc_off = kHeaderBytes;
-  L.tile_off = align_up(L.desc_off + ds.size() * sizeof(split::FusedProb), 256);
-  L.total = align_up(L.tile_off + static_cast<size_t>(tiles) * sizeof(int4), 256);
-  return L;
-}
-
-// Fills the fused descriptors; false if some operand cannot be read by TMA.
-bool fused_descs(const std::vector<GemmDesc> &ds, int layout, split::FusedProb *hd) {
-  for (size_t p = 0; p < ds.size(); ++p) {
-    const GemmDesc &d = ds[p];
-    if (d.m == 0 || d.n == 0) continue;
-    split::FusedProb &q = hd[p];
-    const bool ta = op_trans(d.opA), tb = op_trans(d.opB);
-    q.o.layout = layout;
-    q.o.ta = ta ? 1 : 0;
-    q.o.tb = tb ? 1 : 0;
-    q.o.conj_a = op_conj(d.opA) ? 0xEu : 0u;
-    q.o.conj_b = op_conj(d.opB) ? 0xEu : 0u;
-    q.g.m = d.m;
-    q.g.n = d.n;
-    q.g.num_kb = static_cast<int>((d.k + split::FKQ - 1) / split::FKQ);
-    q.g.num_mt = static_cast<int>((d.m + split::BM - 1) / split::BM);
-    q.g.num_nt = static_cast<int>((d.n + split::BNQ - 1) / split::BNQ);
-    q.g.layout = layout;
-    q.g.beta_zero = d.beta_zero ? 1 : 0;
-    q.g.c_vec4 = (reinterpret_cast<uintptr_t>(d.C) % 16 == 0) ? 1 : 0;
-    q.g.C = static_cast<float *>(d.C);
-    q.g.ldc = d.ldc;
-    q.g.psC = d.psc;
-    for (int c = 0; c < 4; ++c) {
-      q.g.alpha[c] = static_cast<float>(d.alpha[c]);
-      q.g.beta[c] = static_cast<float>(d.beta[c]);
-    }
-    if (d.k > 0) {
-      if (!encode_fp32_operand(&q.tmA, d.A, layout, ta ? split::FKQ : split::BM,
-                               ta ? split::BM : split::FKQ))
-        return false;
-      if (!encode_fp32_operand(&q.tmB, d.B, layout, tb ? split::BNQ : split::FKQ,
-                               tb ? split::FKQ : split::BNQ))
-        return false;
-    }
-  }
-  return true;
-}
-
-int set_fused_smem() {
-  static bool done[64];
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) return QGEMM_ERR_UNSUPPORTED;
-  if (!done[dev]) {
-    if (cudaFuncSetAttribute(split::fused_kernel<GroupedErr, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(split::kFusedSmemBytes)) != cudaSuccess) {
-      cudaGetLastError();
-      return QGEMM_ERR_CUDA;
-    }
-    done[dev] = true;
-  }
-  return QGEMM_SUCCESS;
-}
-
-// Returns QGEMM_ERR_UNSUPPORTED (before touching the workspace) when some
-// operand is not TMA-addressable; the caller then takes the pre-pass path.
-int prepare_fused(const std::vector<GemmDesc> &ds, int layout, unsigned char *ws,
-                  size_t ws_bytes, cudaStream_t s, qgemm_grouped_plan *plan) {
-  const FusedLayout L = layout_fused(ds);
-  if (L.tiles > 0x7fffffff) return QGEMM_ERR_UNSUPPORTED;
-  std::vector<unsigned char> host(L.total - L.desc_off, 0);
-  auto *hd = reinterpret_cast<split::FusedProb *>(host.data());
-  if (!fused_descs(ds, layout, hd)) return QGEMM_ERR_UNSUPPORTED;
-  if (ws_bytes < L.total) return -6;
-  int rc = set_fused_smem();
-  if (rc) return rc;
-  std::vector<int4> tiles;
-  std::vector<int> tile_kb;
-  for (size_t p = 0; p < ds.size(); ++p) {
-    const GemmDesc &d = ds[p];
-    if (d.m == 0 || d.n == 0) continue;
-    for (int a = 0; a < hd[p].g.num_mt; ++a)
-      for (int b = 0; b < hd[p].g.num_nt; ++b) {
-        tiles.push_back(make_int4(static_cast<int>(p), a, b, 0));
-        tile_kb.push_back(hd[p].g.num_kb);
-      }
-  }
-  std::vector<int32_t> order(tiles.size());
-  for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<int32_t>(i);
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int32_t a, int32_t b) { return tile_kb[a] > tile_kb[b]; });
-  int4 *ht = reinterpret_cast<int4 *>(host.data() + (L.tile_off - L.desc_off));
-  for (size_t i = 0; i < order.size(); ++i) ht[i] = tiles[order[i]];
-  if (!host.empty() && cudaMemcpyAsync(ws + L.desc_off, host.data(), host.size(),
-                                       cudaMemcpyHostToDevice, s) != cudaSuccess) {
-    cudaGetLastError();
-    return QGEMM_ERR_CUDA;
-  }
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  plan->workspace_bytes = L.total;
-  plan->tiles = L.tiles;
-  plan->grid = static_cast<int32_t>(std::min<int64_t>(std::max<int64_t>(L.tiles, 1), sms));
-  plan->desc_offset = static_cast<int64_t>(L.desc_off);
-  plan->tile_offset = static_cast<int64_t>(L.tile_off);
-  plan->data_offset = static_cast<int64_t>(L.total);
-  plan->reserved[2] = 1;  // fused
-  return QGEMM_SUCCESS;
-}
-
-int launch_fused(const qgemm_grouped_plan *plan, cudaStream_t s) {
-  unsigned char *ws = static_cast<unsigned char *>(plan->workspace);
-  const auto *probs = reinterpret_cast<const split::FusedProb *>(ws + plan->desc_offset);
-  const auto *tiles = reinterpret_cast<const int4 *>(ws + plan->tile_offset);
-  CUtensorMap none;
-  std::memset(&none, 0, sizeof(none));
-  split::GemmParams g{};
-  split::FusedOps o{};
-  const char *env = std::getenv("QGEMM_SPLIT_CHUNK");
-  const int chunk = (env && std::atoi(env) > 0) ? std::atoi(env) : 2;
-  split::fused_kernel<GroupedErr, true>
-      <<<plan->grid, split::kFusedThreads, split::kFusedSmemBytes, s>>>(
-          none, none, g, o, probs, tiles, static_cast<int>(plan->tiles), chunk, wait_limit_ns());
-  return launch_status();
-}
-
-// The fused path is opt-in (QGEMM_GROUPED_FUSED=1): measured on GB300 its two
-// converter warps limit it below the pre-pass path (4096-problem batch 26.7 vs
-// 47.9 TFLOP/s), and more converter warps do not fit the register budget.
-bool fused_enabled() {
-  const char *e = std::getenv("QGEMM_GROUPED_FUSED");
-  return e && e[0] == '1';
-}
-
 int launch_split(const qgemm_grouped_plan *plan, cudaStream_t s) {
   unsigned char *ws = static_cast<unsigned char *>(plan->workspace);
   const auto *probs = reinterpret_cast<const split::SplitProb *>(ws + plan->desc_offset);
@@ -648,10 +475,8 @@ int launch_split(const qgemm_grouped_plan *plan, cudaStream_t s) {
   CUtensorMap none;
   std::memset(&none, 0, sizeof(none));
   split::GemmParams g{};
-  const char *env = std::getenv("QGEMM_SPLIT_CHUNK");
-  const int chunk = (env && std::atoi(env) > 0) ? std::atoi(env) : 2;
   split::gemm_kernel<GroupedErr, true><<<plan->grid, split::kThreads, split::kSmemBytes, s>>>(
-      none, none, g, probs, tiles, static_cast<int>(plan->tiles), chunk, wait_limit_ns());
+      none, none, g, probs, tiles, static_cast<int>(plan->tiles), wait_limit_ns(), 0);
   return launch_status();
 }
 
@@ -679,11 +504,6 @@ size_t qgemm_grouped_workspace_bytes(const qgemm_problem *problems, int64_t coun
   if (validate_problems(problems, count, layout, precision, &ds)) return 0;
   if (precision == QGEMM_FP64) return layout_fp64(ds).total;
   if (precision == QGEMM_FP64_SLICED_BF16) return sliced_grouped_workspace_bytes(ds);
-  if (fused_enabled()) {
-    std::vector<unsigned char> probe(ds.size() * sizeof(split::FusedProb), 0);
-    if (fused_descs(ds, layout, reinterpret_cast<split::FusedProb *>(probe.data())))
-      return layout_fused(ds).total;
-  }
   return layout_split(ds).total;
 }
 
@@ -706,11 +526,6 @@ int qgemm_grouped_prepare(const qgemm_problem *problems, int64_t count, int layo
     if (precision == QGEMM_FP64_SLICED_BF16)
       return prepare_sliced_grouped(ds, layout, static_cast<unsigned char *>(workspace),
                                     workspace_bytes, static_cast<cudaStream_t>(stream), plan);
-    if (fused_enabled()) {
-      rc = prepare_fused(ds, layout, static_cast<unsigned char *>(workspace), workspace_bytes,
-                         static_cast<cudaStream_t>(stream), plan);
-      if (rc != QGEMM_ERR_UNSUPPORTED) return rc;
-    }
     return prepare_split(ds, layout, static_cast<unsigned char *>(workspace), workspace_bytes,
                          static_cast<cudaStream_t>(stream), plan);
   }
@@ -790,8 +605,7 @@ int qgemm_grouped_launch(const qgemm_grouped_plan *plan, void *stream) {
   if (plan->precision == QGEMM_FP64_SLICED_BF16)
     return launch_sliced_grouped(plan, static_cast<cudaStream_t>(stream));
   if (plan->precision == QGEMM_FP32_SPLIT_BF16)
-    return plan->reserved[2] == 1 ? launch_fused(plan, static_cast<cudaStream_t>(stream))
-                                  : launch_split(plan, static_cast<cudaStream_t>(stream));
+    return launch_split(plan, static_cast<cudaStream_t>(stream));
   rc = set_grouped_smem(plan->layout);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

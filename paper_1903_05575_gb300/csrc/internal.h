@@ -109,6 +109,11 @@ int misc_take_device_error();
 int sliced_take_device_error();
 int fp64m_take_device_error();
 int debug_unsatisfied_wait(uint64_t limit_ns, cudaStream_t stream);
+// One-shot fault injection: the next split-BF16 GEMM launch leaves out the
+// copies of its TMA warp's running stage `stage` and waits at most limit_ns.
+void split_arm_fault(int stage, uint64_t limit_ns);
+// The same for the next FP64 GEMM launch (its first CTA's ring stage `stage`).
+void fp64_arm_fault(int stage, uint64_t limit_ns);
 int probe_peak(int which, double seconds, double *tflops, cudaStream_t stream);
 
 }  // namespace qg

@@ -2,18 +2,18 @@
 // of the paper's library, Sec. 5): C <- alpha op(A) op(B) + beta C with C
 // quaternion and A, B each quaternion, complex (z^0 e0 + z^1 e1) or real.
 //
-// Split-BF16 and digit-sliced paths: the real form C' = A' B' only needs the
-// components the left factor has.  With a complex (real) left factor a, the
-// product a b has (a b)^c = sum_j sign(j, j^c) a^j b^(j^c) over j < 2 (j < 1),
-// so A' keeps 2 (1) columns per kappa and B' the matching 2 (1) rows of its
-// sign expansion: K' = 2k (k), half (a quarter) of the MMAs of the
-// quaternion product.  A quaternion left factor with a narrow right factor
-// is turned around with (AB)^H = B^H A^H (Sec. 2.2): the kernel computes
-// D = op(B)^H op(A)^H with the narrow factor on the left and stores
-// C = conj(D)^T.  The FP64 DMMA path takes the narrow factor on the RIGHT
-// (fp64_mixed.cu: one DMMA spans 4 / width values of kappa), turning a
-// narrow left factor around the same way; when both are narrow the left one
-// is copied as a quaternion matrix into the workspace.
+// Split-BF16 path: the component-plane kernel (split_core.cuh) sums the real
+// products A^p (B^j)^T over the planes each factor has, so a complex (real)
+// factor on either side has 2 (1) planes: half (a quarter) of the MMAs of the
+// quaternion product.  Digit-sliced path: its real form C' = A' B' only needs
+// the components the left factor has (A' keeps 2 (1) columns per kappa and
+// B' the matching rows of its sign expansion, K' = 2k (k)); a quaternion left
+// factor with a narrow right factor is turned around with (AB)^H = B^H A^H
+// (Sec. 2.2): the kernel computes D = op(B)^H op(A)^H with the narrow factor
+// on the left and stores C = conj(D)^T.  The FP64 DMMA path takes the narrow
+// factor on the RIGHT (fp64_mixed.cu: one DMMA spans 4 / width values of
+// kappa), turning a narrow left factor around the same way; when both are
+// narrow the left one is copied as a quaternion matrix into the workspace.
 #include <cstring>
 
 #include "common.cuh"
@@ -73,8 +73,9 @@ int op_conjtrans(int op) {
   }
 }
 
-// Validated descriptor of a mixed product.  Tensor-core precisions: the
-// narrow factor goes to the left (turned around when it is B).
+// Validated descriptor of a mixed product.  FP64: the narrow factor goes to
+// the right; digit-sliced: to the left (turned around when needed);
+// split-BF16: either side as it is.
 int mixed_desc(int typeA, int typeB, int opA, int opB, int64_t m, int64_t n, int64_t k,
                const double *alpha, const void *A, int64_t lda, int64_t psA, const void *B,
                int64_t ldb, int64_t psB, const double *beta, void *C, int64_t ldc, int64_t psC,
@@ -103,7 +104,10 @@ int mixed_desc(int typeA, int typeB, int opA, int opB, int64_t m, int64_t n, int
     if (typeA != 0 && typeB == 0) turn_around(d);
     return 0;
   }
-  // tensor-core precisions: the narrow factor on the left
+  // split-BF16: the component-plane kernel takes a narrow factor on either
+  // side (fewer planes), nothing to rearrange
+  if (precision == QGEMM_FP32_SPLIT_BF16) return 0;
+  // digit-sliced: the narrow factor on the left
   if (typeA != 0) {
     d->kwidth = kWidth[typeA];
   } else if (typeB != 0) {

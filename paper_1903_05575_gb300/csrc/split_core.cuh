@@ -2,35 +2,48 @@
 // device code shared by the single-problem path (split_bf16.cu) and the
 // grouped path (grouped.cu).
 //
-// Real form.  With a = op(A)_{i kappa}, b = op(B)_{kappa n}, the Hamilton
-// product (Sec. 2.1, Eq. quaternion_prod) is linear in a:
-//     (a b)^c = sum_j sign(j, j xor c) a^j b^(j xor c),
-// sign(p, q) the sign of the basis product e_p e_q (Eq. quaternion_alg).  So
-//     C'(m x 4n) = A'(m x 4k) * B'(4k x 4n),
-//     A'[i][4 kappa + j]         = a^j                                (A as stored)
-//     B'[4 kappa + j][4 n + c]   = sign(j, j xor c) b^(j xor c)       (B expanded)
-//     C'[i][4 n + c]             = (op(A) op(B))_{i n}^c
-// which is one real GEMM with exactly the 16 m n k multiplies of the
-// quaternion product; conjugation of A or B only flips signs of A' / B'.
+// Component form.  With a = op(A)_{i kappa} and b = op(B)_{kappa n}, the
+// Hamilton product (Sec. 2.1, Eq. quaternion_prod) is
+//     (a b)^c = sum over p xor j = c of sign(p, j) a^p b^j,
+// sign(p, j) the sign of the basis product e_p e_j (Eq. quaternion_alg).  So
+// component c of op(A) op(B) is the signed sum of the four real products
+// A^p (B^j)^T with p xor j = c, where X^s is the real matrix of component s
+// of X (the plane of Eq. quaternion_mat_def): sixteen real products, exactly
+// the 16 m n k multiplies of the quaternion product.  The planes are stored
+// K-major (BF16 terms, below) and each component c of the result accumulates
+// in its own tensor-memory region; the sign is the MMA instruction's negate
+// bit, so no operand is ever sign-expanded.  The MMAs that share one A plane
+// and one sign take it from the tensor core's operand collector (fill / use
+// / lastuse), so shared memory supplies it once per group.  A complex or
+// real factor simply has fewer planes.
 //
-// Precision.  Each FP32 value x is split into three BF16 terms by
-// round-to-nearest: hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid)
-// (both differences exact in FP32).  The six leading term products
-// hh, hm, mh, hl, mm, lh run on tcgen05.mma kind::f16 (BF16 in, FP32 out in
-// tensor memory); mid*lo, lo*mid and lo*lo (relative size 2^-24) are dropped.
-// The FP32 tensor-memory accumulator is drained every `chunk` k-blocks into a
-// register accumulator (two TMEM buffers, so the MMAs never wait for the
-// drain); the tensor core's in-accumulator additions are biased, so the
-// chunk is short and the register sum takes the rest.  The epilogue forms
-// alpha P and beta C in FP32 and sums them in FP64 before the one rounding.
+// Scalars.  alpha is applied to op(A) by the pre-pass, in double-float
+// arithmetic (pairs of FP32 with error-free products and sums), before the
+// split: (alpha op(A)) op(B) = alpha (op(A) op(B)) (associativity; the
+// scalar acts from the left, Sec. 2.2).  beta C is added by the epilogue in
+// the same arithmetic, with one final rounding.
+//
+// Precision.  Each value x (an FP32 input, or alpha x in double-float) is
+// split by round-to-nearest into three BF16 terms hi + mid + lo, with a
+// residual below 2^-27 |x|.  The six leading term products hh, hm, mh, hl, mm,
+// lh run on tcgen05.mma kind::f16 (BF16 in, FP32 accumulate in tensor memory);
+// mid lo, lo mid and lo lo (below 2^-27 of a product) are dropped.  The
+// accumulator is drained every chunk of K into a register sum by a
+// compensated addition (TwoSum) whose rounding error is written back into the
+// tensor-memory accumulator, where the next chunk of the same buffer adds
+// onto it.  So the running sum keeps the accuracy of the chunk sums instead
+// of losing one FP32 rounding of the whole sum per chunk; GB300's FP64 pipe is
+// 64 times narrower than its FP32 pipe, so the FP64-class steps run as
+// error-free FP32 transformations.
 //
 // Kernel.  Persistent: each CTA walks tiles blockIdx.x, +gridDim.x, ...; one
-// warp issues TMA loads (3-D boxes: K x rows x term, 64-byte swizzle) into a
-// 3-stage ring, one warp issues the MMAs (M=128, N=256, K=16) into one of two
-// TMEM accumulators and commits them to mbarriers, eight warps drain TMEM and
-// run the epilogue of a tile while the MMAs of the next one proceed.  Ring
-// slots, barrier phases and TMEM buffers are indexed by running counters that
-// continue across tiles.  Every wait is bounded.
+// warp issues TMA loads (4-D boxes: kappa x rows x planes x terms, 32-byte
+// swizzle) into a 3-stage ring, one warp issues the MMAs (M = 128, N <= 64,
+// K = 16) into one of two TMEM accumulator sets and commits them to
+// mbarriers, eight warps drain TMEM and run the epilogue of a tile while the
+// MMAs of the next one proceed.  Ring slots, barrier phases and TMEM buffers
+// are indexed by running counters that continue across tiles.  Every wait is
+// bounded.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -41,25 +54,34 @@ namespace split {
 
 // ---------------------------------------------------------------- sizes ---
 constexpr int BM = 128;            // rows of C per tile (TMEM lanes)
-constexpr int BN = 256;            // columns of C' per tile = 64 quaternion columns
-constexpr int BNQ = BN / 4;
-constexpr int BK = 32;             // reals of K per stage (64 bytes: one swizzle row)
+constexpr int BNQ = 64;            // quaternion columns of C per tile (largest MMA N)
+constexpr int KQ = 16;             // kappa per stage: one MMA K step (32-byte rows)
 constexpr int STAGES = 3;
 constexpr int TERMS = 3;
+constexpr int PLANES = 4;
+constexpr int kChunk = 1;          // stages per TMEM drain
 constexpr int kEpiWarps = 8;
-constexpr int kThreads = 64 + 32 * kEpiWarps;  // warp 0 TMA, warp 1 MMA, 2..9 drain/epilogue
-constexpr uint32_t kATermBytes = BM * BK * 2;  // 8 KB
-constexpr uint32_t kBTermBytes = BN * BK * 2;  // 16 KB
-constexpr uint32_t kStageA = TERMS * kATermBytes;
-constexpr uint32_t kStageB = TERMS * kBTermBytes;
-constexpr uint32_t kStageBytes = kStageA + kStageB;  // 72 KB
-constexpr uint32_t kTmemCols = 2 * BN;               // two accumulator buffers
+// warp 0 TMA, warp 1 MMA, warps 2-3 idle (warpgroup 0), warps 4..11 drain /
+// epilogue (warpgroups 1 and 2)
+constexpr int kThreads = 128 + 32 * kEpiWarps;
+// Registers per thread after the split of the launch's 384 x 168: warpgroup
+// 0 gives up to kRegsCtl, the drain warpgroups take kRegsDrain (128 x 64 +
+// 256 x 216 = 63488 <= 64512; per SM sub-partition 64 + 2 x 216 = 496 <= 512).
+constexpr int kRegsCtl = 64;
+constexpr int kRegsDrain = 216;
+static_assert(128 * kRegsCtl + 32 * kEpiWarps * kRegsDrain <= kThreads * 168, "register split");
+constexpr uint32_t kAPlaneBytes = BM * KQ * 2;   // 4 KB
+constexpr uint32_t kBPlaneBytes = BNQ * KQ * 2;  // 2 KB
+constexpr uint32_t kStageA = TERMS * PLANES * kAPlaneBytes;  // 48 KB
+constexpr uint32_t kStageB = TERMS * PLANES * kBPlaneBytes;  // 24 KB
+constexpr uint32_t kStageBytes = kStageA + kStageB;           // 72 KB
+constexpr uint32_t kBufCols = PLANES * BNQ;                   // one accumulator set
+constexpr uint32_t kTmemCols = 2 * kBufCols;                  // two sets
 constexpr size_t kSmemBytes = 1024 + STAGES * kStageBytes + 256;
-constexpr int kGroupM = 8;                           // row tiles per raster group
-
-// The six kept term products (A term, B term): hh, hm, mh, hl, mm, lh.
-__host__ __device__ constexpr int term_a(int tp) { return tp == 2 || tp == 4 ? 1 : (tp == 5 ? 2 : 0); }
-__host__ __device__ constexpr int term_b(int tp) { return tp == 1 || tp == 4 ? 1 : (tp == 3 ? 2 : 0); }
+constexpr int kGroupM = 8;                                    // row tiles per raster group
+// The largest quaternion k: a share's 32-bit stage counters and the TMA
+// coordinates stay in range.
+constexpr int64_t kMaxK = int64_t(1) << 30;
 
 // ------------------------------------------------------ tcgen05 helpers ---
 // Shared-memory matrix descriptor, K-major, 64-byte swizzle: 8-row groups
@@ -92,6 +114,23 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// The same MMA with the A operand taken into (fill), reused from (use) or
+// released from (lastuse) the tensor core's operand collector: consecutive
+// MMAs that share A then read it from shared memory once.
+#define QG_UMMA_COLLECTOR(NAME, QUAL)                                                       \
+  __device__ __forceinline__ void NAME(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,     \
+                                       uint32_t idesc, uint32_t accumulate) {               \
+    asm volatile(                                                                           \
+        "{\n\t.reg .pred p;\n\t"                                                        \
+        "setp.ne.b32 p, %4, 0;\n\t"                                                       \
+        "tcgen05.mma.cta_group::1.kind::f16.collector::a::" QUAL " [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem), \
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)                                 \
+        : "memory");                                                                        \
+  }
+QG_UMMA_COLLECTOR(umma_bf16_fill, "fill")
+QG_UMMA_COLLECTOR(umma_bf16_use, "use")
+QG_UMMA_COLLECTOR(umma_bf16_lastuse, "lastuse")
+#undef QG_UMMA_COLLECTOR
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -143,43 +182,127 @@ __device__ __forceinline__ bool elect_one() {
   return pred != 0;
 }
 
-// --------------------------------------------------------- split helper ---
-struct Split3 {
-  __nv_bfloat16 t[3];
-};
-__device__ __forceinline__ Split3 split3(float x) {
-  Split3 s;
-  s.t[0] = __float2bfloat16_rn(x);
-  const float r1 = x - __bfloat162float(s.t[0]);
-  s.t[1] = __float2bfloat16_rn(r1);
-  const float r2 = r1 - __bfloat162float(s.t[1]);
-  s.t[2] = __float2bfloat16_rn(r2);
-  return s;
+// K-major, 32-byte swizzle (one 16-element BF16 row per 32 bytes): 8-row
+// groups 256 bytes apart (SBO), leading offset unused, descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFF);
+  d |= static_cast<uint64_t>(1) << 16;                  // LBO (ignored for swizzled K-major)
+  d |= static_cast<uint64_t>(256 >> 4) << 32;           // SBO
+  d |= static_cast<uint64_t>(1) << 46;                  // version
+  d |= static_cast<uint64_t>(6) << 61;                  // SWIZZLE_32B
+  return d;
+}
+// Instruction-descriptor bit that negates the B operand of one MMA.
+constexpr uint32_t kNegB = 1u << 14;
+
+// 32 consecutive 32-bit columns of this thread's TMEM lane <- v.  The caller
+// waits (tmem_st_wait) before it hands the columns to the MMAs.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
+      "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
+      "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+      "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+      "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
+      "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      : "memory");
+}
+// 16 consecutive 32-bit columns of this thread's TMEM lane (load with its
+// wait; store without).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// ------------------------------------------------ double-float helpers ---
+// Error-free transformations on FP32 (Knuth's TwoSum; the product error by
+// one FMA).  The _rn intrinsics are never contracted or reassociated.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float ap = __fsub_rn(s, bp);
+  e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+// (hi, lo) += (sh + sl) x: the product sh x exactly (value and FMA error),
+// sl x in FP32, the sum by TwoSum; lo collects the small parts.
+__device__ __forceinline__ void df_fma(float &hi, float &lo, float sh, float sl, float x) {
+  const float p = __fmul_rn(sh, x);
+  float e = __fmaf_rn(sh, x, -p);
+  e = __fmaf_rn(sl, x, e);
+  float s, e2;
+  two_sum(hi, p, s, e2);
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(e, e2));
+}
+// Three BF16 terms of the double-float value hi + lo (round to nearest):
+// hi - t0 is exact in FP32, so the residual after three terms is below
+// 2^-27 |hi|.
+__device__ __forceinline__ void split3_df(float hi, float lo, __nv_bfloat16 (&t)[3]) {
+  t[0] = __float2bfloat16_rn(hi);
+  const float r1 = __fadd_rn(__fsub_rn(hi, __bfloat162float(t[0])), lo);
+  t[1] = __float2bfloat16_rn(r1);
+  t[2] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(t[1])));
 }
 
 // ----------------------------------------------------------- pre-pass ---
 // One 32 x 32 tile of the op-matrix X (rows r = i for A or n for B; columns
-// kappa), read coalesced from the stored layout through shared memory, split,
-// and written K-major with kw components per kappa (4; 2 or 1 when the left
-// operand is complex or real, whose missing components are zero):
-//   A:  A'_t[r][kw kappa + j]                            j < kw
-//   B:  B'_t[4 r + c][kw kappa + j] = sign(j, j^c) * t(b^(j^c))
-// (row pitch kp).  Columns kappa >= kq up to kp/kw are zeros (K padding).
-// An operand stores `width` components per element (4, 2 or 1); the rest
-// read as zero.
+// kappa), read coalesced from the stored layout through shared memory,
+// conjugated when the op says so, multiplied by the pre-pass scalar s (alpha
+// on the left for A; conj(alpha) on the right for the B side of a problem the
+// grouped path turned around), split into three BF16 terms and written as
+// K-major planes:
+//   out[((t * planes + c) * rows + r) * kp + kappa] = term t of (s x)^c.
+// Columns kappa >= kq are not written (the tensor maps end at kq and read
+// zeros beyond).  An operand stores `width` components per element; the
+// others read as zero.
+enum { kScaleNone = 0, kScaleReal = 1, kScaleLeft = 2, kScaleRight = 3 };
 struct PrepArgs {
   const float *X;
   int64_t ld, ps;       // stored leading dimension, plane stride
   int64_t rows;         // rows of the op-matrix (m for A, n for B)
   int64_t kq;           // quaternion K
-  int64_t kp;           // padded real K (multiple of BK)
-  int64_t term_stride;  // elements between terms in the output
+  int64_t kp;           // kappa pitch of the output (multiple of 8)
   __nv_bfloat16 *out;
   int layout;
   int row_contig;       // stored row index == op row (contiguous along r)
-  uint32_t negmask;     // bit j: negate component j of the input (conjugation)
+  int conj;             // op C or H: negate components 1..3
   int width;            // components stored per element
-  int kw;               // components per kappa in the output
+  int planes;           // planes written (1, 2 or 4)
+  int smode;            // kScale*
+  float s_hi[4], s_lo[4];
 };
 
 __device__ __forceinline__ float4 load_elem(const PrepArgs &p, int64_t sr, int64_t sc) {
@@ -198,20 +321,33 @@ __device__ __forceinline__ float4 load_elem(const PrepArgs &p, int64_t sr, int64
   return make_float4(v[0], v[1], v[2], v[3]);
 }
 
-template <int KW>
-__device__ __forceinline__ void store_terms(__nv_bfloat16 *dst, const __nv_bfloat16 (&w)[4]) {
-  if (KW == 4) {
-    *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(w);
-  } else if (KW == 2) {
-    *reinterpret_cast<uint32_t *>(dst) = *reinterpret_cast<const uint32_t *>(w);
-  } else {
-    dst[0] = w[0];
+// (hi, lo)^c of s x (kScaleLeft), x s (kScaleRight) or s0 x (kScaleReal).
+__device__ __forceinline__ void scale_df(const PrepArgs &p, const float (&x)[4], float (&hi)[4],
+                                         float (&lo)[4]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    hi[c] = 0.f;
+    lo[c] = 0.f;
   }
+  if (p.smode == kScaleReal) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) df_fma(hi[c], lo[c], p.s_hi[0], p.s_lo[0], x[c]);
+    return;
+  }
+  const bool left = p.smode == kScaleLeft;
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int q = c ^ j;  // scalar component q meets x^j
+      const bool neg = left ? basis_sign(q, j) < 0 : basis_sign(j, q) < 0;
+      df_fma(hi[c], lo[c], neg ? -p.s_hi[q] : p.s_hi[q], neg ? -p.s_lo[q] : p.s_lo[q], x[j]);
+    }
 }
 
-template <bool IS_B, int KW>
-__device__ __forceinline__ void prep_tile_kw(const PrepArgs &p, int64_t rt, int64_t kt,
-                                             float4 (*tile)[33]) {
+template <bool IS_B>
+__device__ __forceinline__ void prep_tile(const PrepArgs &p, int64_t rt, int64_t kt,
+                                          float4 (*tile)[33]) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   const int64_t r0 = rt * 32, k0 = kt * 32;
 #pragma unroll
@@ -223,81 +359,69 @@ __device__ __forceinline__ void prep_tile_kw(const PrepArgs &p, int64_t rt, int6
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (r < p.rows && kq < p.kq) {
       v = load_elem(p, p.row_contig ? r : kq, p.row_contig ? kq : r);
-      if (p.negmask & 2u) v.y = -v.y;
-      if (p.negmask & 4u) v.z = -v.z;
-      if (p.negmask & 8u) v.w = -v.w;
+      if (p.conj) {
+        v.y = -v.y;
+        v.z = -v.z;
+        v.w = -v.w;
+      }
     }
     tile[kk][rr] = v;
   }
   __syncthreads();
+  const int64_t plane_stride = p.rows * p.kp;
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     const int kk = tx, rr = ty + 8 * s;
     const int64_t r = r0 + rr, kq = k0 + kk;
-    if (r >= p.rows || KW * kq >= p.kp) continue;
+    if (r >= p.rows || kq >= p.kq) continue;
     const float4 v = tile[kk][rr];
-    const float comp[4] = {v.x, v.y, v.z, v.w};
-    Split3 sp[4];
+    const float x[4] = {v.x, v.y, v.z, v.w};
+    float hi[4], lo[4];
+    if (p.smode == kScaleNone) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) sp[j] = split3(comp[j]);
-    if (!IS_B) {
-#pragma unroll
-      for (int t = 0; t < TERMS; ++t) {
-        __align__(8) __nv_bfloat16 w[4] = {sp[0].t[t], sp[1].t[t], sp[2].t[t], sp[3].t[t]};
-        store_terms<KW>(p.out + t * p.term_stride + r * p.kp + KW * kq, w);
+      for (int c = 0; c < 4; ++c) {
+        hi[c] = x[c];
+        lo[c] = 0.f;
       }
     } else {
+      scale_df(p, x, hi, lo);
+    }
+    __nv_bfloat16 *dst = p.out + r * p.kp + kq;
 #pragma unroll
-      for (int t = 0; t < TERMS; ++t)
+    for (int c = 0; c < 4; ++c) {
+      if (c >= p.planes) break;
+      __nv_bfloat16 t[3];
+      split3_df(hi[c], lo[c], t);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          __align__(8) __nv_bfloat16 w[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int q = j ^ c;
-            const __nv_bfloat16 x = sp[q].t[t];
-            w[j] = basis_sign(j, q) < 0 ? __hneg(x) : x;
-          }
-          store_terms<KW>(p.out + t * p.term_stride + (4 * r + c) * p.kp + KW * kq, w);
-        }
+      for (int tt = 0; tt < TERMS; ++tt) dst[(tt * p.planes + c) * plane_stride] = t[tt];
     }
   }
-}
-
-template <bool IS_B>
-__device__ __forceinline__ void prep_tile(const PrepArgs &p, int64_t rt, int64_t kt,
-                                          float4 (*tile)[33]) {
-  if (p.kw == 4)
-    prep_tile_kw<IS_B, 4>(p, rt, kt, tile);
-  else if (p.kw == 2)
-    prep_tile_kw<IS_B, 2>(p, rt, kt, tile);
-  else
-    prep_tile_kw<IS_B, 1>(p, rt, kt, tile);
 }
 
 // --------------------------------------------------------- GEMM params ---
 // Per-problem parameters of the GEMM kernel.
 struct GemmParams {
   int64_t m, n;           // quaternion sizes of C
-  int num_kb;             // k-blocks of BK reals (0: C <- beta C)
+  int num_kb;             // stages of KQ kappa (0: C <- beta C)
   int num_mt, num_nt;     // tiles
+  int pa, pb;             // planes of the A and B operands (1, 2 or 4)
   int layout;
-  int beta_zero;
+  int beta_zero, beta_real;
   int c_vec4;             // interleaved C 16-byte aligned: float4 access
   float *C;
   int64_t ldc, psC;
-  float alpha[4], beta[4];
+  float beta_hi[4], beta_lo[4];  // beta as double-float pairs
   int tri;                // 0 full; 1 lower (row >= col) only; 2 upper; real diagonal
   int swap;               // 1: the kernel computed D = (op(A) op(B))^H; store C = conj(D)^T
   int krange;             // k-range of a tile when op(A) or op(B) is triangular (GemmDesc)
   // K split (single problems): tile t of the launch is share z = t / (num_mt
-  // num_nt) of its tile's k-blocks, whose product P (FP32) goes to part +
-  // z m n 4 (dense, interleaved, leading dimension m) for a second kernel.
+  // num_nt) of its tile's stages, whose product P (FP32) goes to part + z m n
+  // 4 (dense, interleaved, leading dimension m) for a second kernel.
   int ksplit;             // 0 or 1: no split
   float *part;
 };
 
-// k-blocks [lo, hi) of tile (mt, nt), share z: all of K, or the part where a
+// Stages [lo, hi) of tile (mt, nt), share z: all of K, or the part where a
 // triangular operand can be nonzero for the tile's rows or columns; then
 // share z of it when the problem splits K.
 __host__ __device__ inline void kb_range(const GemmParams &g, int mt, int nt, int z, int &lo,
@@ -306,13 +430,13 @@ __host__ __device__ inline void kb_range(const GemmParams &g, int mt, int nt, in
   hi = g.num_kb;
   const int64_t rq0 = static_cast<int64_t>(mt) * BM, cq0 = static_cast<int64_t>(nt) * BNQ;
   if (g.krange == 1) {
-    const int64_t e = (4 * (rq0 + BM) + BK - 1) / BK;
+    const int64_t e = (rq0 + BM + KQ - 1) / KQ;
     if (e < hi) hi = static_cast<int>(e);
   }
-  if (g.krange == 2) lo = static_cast<int>(4 * rq0 / BK);
-  if (g.krange == 3) lo = static_cast<int>(4 * cq0 / BK);
+  if (g.krange == 2) lo = static_cast<int>(rq0 / KQ);
+  if (g.krange == 3) lo = static_cast<int>(cq0 / KQ);
   if (g.krange == 4) {
-    const int64_t e = (4 * (cq0 + BNQ) + BK - 1) / BK;
+    const int64_t e = (cq0 + BNQ + KQ - 1) / KQ;
     if (e < hi) hi = static_cast<int>(e);
   }
   if (lo > hi) lo = hi;
@@ -324,10 +448,18 @@ __host__ __device__ inline void kb_range(const GemmParams &g, int mt, int nt, in
   }
 }
 
+// MMA width of tile column nt: the valid quaternion columns rounded up to
+// 16 (the M = 128 granule), at most BNQ.
+__host__ __device__ inline int tile_ncols(const GemmParams &g, int nt) {
+  const int64_t rem = g.n - static_cast<int64_t>(nt) * BNQ;
+  const int64_t w = rem >= BNQ ? BNQ : ((rem + 15) / 16) * 16;
+  return static_cast<int>(w);
+}
+
 // Device descriptor of one problem of a grouped batch.
 struct alignas(128) SplitProb {
-  CUtensorMap tmA;  // A' : (kp, m, 3) bf16
-  CUtensorMap tmB;  // B' : (kp, 4n, 3) bf16
+  CUtensorMap tmA;  // A planes: (kq, m, pa, 3) bf16
+  CUtensorMap tmB;  // B planes: (kq, n, pb, 3) bf16
   PrepArgs pa, pb;
   GemmParams g;
 };
@@ -414,8 +546,8 @@ __device__ __forceinline__ float *c_elem(const GemmParams &g, int64_t ci, int64_
 
 // Prefetches into L2 the C elements that epilogue() will read for row i and
 // the 32 quaternion columns from nbase (only those inside C).  Issued when a
-// tile's first chunk reaches the drain, so the epilogue's reads of C hit L2
-// instead of waiting on DRAM one element after another.
+// tile starts, so the epilogue's reads of C hit L2 instead of waiting on DRAM
+// one element after another.
 __device__ __forceinline__ void prefetch_c(const GemmParams &g, int64_t i, int64_t nbase) {
   if (g.beta_zero || i >= g.m) return;
 #pragma unroll 4
@@ -433,21 +565,15 @@ __device__ __forceinline__ void prefetch_c(const GemmParams &g, int64_t i, int64
 }
 
 // Epilogue of one tile for one drain thread: row i, 32 quaternion columns
-// starting at nbase, accumulated P in acc.  out = alpha P + beta C (left
-// products); alpha P and beta C in FP32, their sum in FP64, one rounding.
-// C is read in batches of kCBatch elements, all loads of a batch before its
-// stores (a larger batch does not fit the drain warps' register budget).
+// starting at nbase, accumulated P in acc[32 c + q] (component c, column q).
+// out = P + beta C (beta on the left), in double-float with one rounding.  C
+// is read in batches of kCBatch elements, all loads of a batch before its
+// stores.
 constexpr int kCBatch = 4;
 __device__ __forceinline__ void epilogue(const GemmParams &g, int64_t i, int64_t nbase,
                                          const float (&acc)[128]) {
   if (i >= g.m) return;
   if (g.tri == 2 && nbase + 31 < i) return;
-  float al[4], be[4];
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    al[s] = g.alpha[s];
-    be[s] = g.beta[s];
-  }
 #pragma unroll
   for (int qb = 0; qb < 32; qb += kCBatch) {
     float cin[kCBatch][4];
@@ -475,7 +601,7 @@ __device__ __forceinline__ void epilogue(const GemmParams &g, int64_t i, int64_t
       const int64_t nn = nbase + q;
       if (nn >= g.n) continue;
       if ((g.tri == 1 && i < nn) || (g.tri == 2 && i > nn)) continue;
-      float P[4] = {acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]};
+      float P[4] = {acc[q], acc[32 + q], acc[64 + q], acc[96 + q]};
       const int64_t ci = g.swap ? nn : i, cj = g.swap ? i : nn;
       if (g.swap) {
         P[1] = -P[1];
@@ -485,17 +611,21 @@ __device__ __forceinline__ void epilogue(const GemmParams &g, int64_t i, int64_t
       float out[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        float ap = 0.f, bc = 0.f;
+        float hi = P[c], lo = 0.f;
+        if (!g.beta_zero) {
+          if (g.beta_real) {
+            df_fma(hi, lo, g.beta_hi[0], g.beta_lo[0], cin[u][c]);
+          } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int s = c ^ j;  // the sign is a compile-time constant here
-          const bool neg = basis_sign(s, j) < 0;
-          ap = fmaf(neg ? -al[s] : al[s], P[j], ap);
-          bc = fmaf(neg ? -be[s] : be[s], cin[u][j], bc);
+            for (int j = 0; j < 4; ++j) {
+              const int s = c ^ j;  // the sign is a compile-time constant here
+              const bool neg = basis_sign(s, j) < 0;
+              df_fma(hi, lo, neg ? -g.beta_hi[s] : g.beta_hi[s],
+                     neg ? -g.beta_lo[s] : g.beta_lo[s], cin[u][j]);
+            }
+          }
         }
-        out[c] = g.beta_zero
-                     ? ap
-                     : static_cast<float>(static_cast<double>(ap) + static_cast<double>(bc));
+        out[c] = __fadd_rn(hi, lo);
       }
       if (g.tri && i == nn) out[1] = out[2] = out[3] = 0.f;  // Hermitian diagonal is real
       float *dst0 = c_elem(g, ci, cj);
@@ -524,19 +654,110 @@ __device__ __forceinline__ void store_partial(const GemmParams &g, int64_t i, in
     const int64_t nn = nbase + q;
     if (nn >= g.n) break;
     *reinterpret_cast<float4 *>(slab + 4 * (i + nn * g.m)) =
-        make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        make_float4(acc[q], acc[32 + q], acc[64 + q], acc[96 + q]);
   }
+}
+
+// Planes j of B whose product with A plane p has the sign of group sg (0:
+// positive, 1: negative): bit j of the mask.
+__host__ __device__ constexpr uint32_t sign_group(int p, int sg) {
+  uint32_t m = 0;
+  for (int j = 0; j < PLANES; ++j)
+    if ((basis_sign(p, j) < 0) == (sg == 1)) m |= 1u << j;
+  return m;
+}
+
+__host__ __device__ constexpr int low_bit(uint32_t m) {
+  return (m & 1u) ? 0 : (m & 2u) ? 1 : (m & 4u) ? 2 : 3;
+}
+__host__ __device__ constexpr int high_bit(uint32_t m) {
+  return (m & 8u) ? 3 : (m & 4u) ? 2 : (m & 2u) ? 1 : 0;
+}
+
+// The MMAs of one stage into accumulator set d0 (component c at d0 + c BNQ),
+// for PA planes of A and PB of B: every A term ta and plane p times B terms
+// tb (ta + tb <= 2: hh, hm, hl, mh, mm, lh) and planes j go to component
+// p xor j with the sign of e_p e_j.
+//  - Order: the small term products (lh; mh, mm; hl, hm) before hh, so most
+//    of the tensor core's accumulator additions happen while the sum is
+//    about 2^-8 of its final size (its additions round at that scale).
+//  - Collector: the MMAs of one pass that share A(ta, p) and a sign form a
+//    group that reads A from shared memory once; the negation is taken when
+//    A enters the collector (measured: a negate bit on a collector `use` has
+//    no effect), so positive and negative products are separate groups.
+//  - The first MMA into a component overwrites it unless `carry` (the
+//    component holds the error written back by the drain).
+// Descriptors are the stage's base descriptors plus compile-time offsets.
+template <int PA, int PB>
+__device__ __forceinline__ void issue_stage(uint32_t d0, uint64_t adesc, uint64_t bdesc,
+                                            uint32_t idesc_n, bool carry) {
+  // passes: (A term, first B term, last B term)
+  constexpr int kPassTa[4] = {2, 1, 0, 0};
+  constexpr int kPassTb0[4] = {0, 0, 1, 0};
+  constexpr int kPassTb1[4] = {0, 1, 2, 0};
+  uint32_t touched = 0;
+#pragma unroll
+  for (int pass = 0; pass < 4; ++pass) {
+    const int ta = kPassTa[pass];
+#pragma unroll
+    for (int p = 0; p < PA; ++p) {
+      const uint64_t ad = adesc + (((ta * PA + p) * kAPlaneBytes) >> 4);
+#pragma unroll
+      for (int sg = 0; sg < 2; ++sg) {
+        const uint32_t grp = sign_group(p, sg) & ((1u << PB) - 1u);
+        if (grp == 0) continue;
+        const int jfirst = low_bit(grp), jlast = high_bit(grp);
+        const uint32_t id = idesc_n | (sg ? kNegB : 0u);
+#pragma unroll
+        for (int tb = kPassTb0[pass]; tb <= kPassTb1[pass]; ++tb)
+#pragma unroll
+          for (int j = 0; j < PB; ++j) {
+            if (!((grp >> j) & 1u)) continue;
+            const int c = p ^ j;
+            const uint64_t bd = bdesc + (((tb * PB + j) * kBPlaneBytes) >> 4);
+            const uint32_t acc = (carry || ((touched >> c) & 1u)) ? 1u : 0u;
+            touched |= 1u << c;
+            const uint32_t d = d0 + c * BNQ;
+            const bool first = tb == kPassTb0[pass] && j == jfirst;
+            const bool last = tb == kPassTb1[pass] && j == jlast;
+            if (first && last)
+              umma_bf16(d, ad, bd, id, acc);
+            else if (first)
+              umma_bf16_fill(d, ad, bd, id, acc);
+            else if (last)
+              umma_bf16_lastuse(d, ad, bd, id, acc);
+            else
+              umma_bf16_use(d, ad, bd, id, acc);
+          }
+      }
+    }
+  }
+}
+
+// issue_stage for the plane counts of a problem (1, 2 or 4 each).
+__device__ __forceinline__ void issue_stage_planes(int pa, int pb, uint32_t d0, uint64_t adesc,
+                                                   uint64_t bdesc, uint32_t idesc_n, bool carry) {
+#define QG_ISSUE(A_, B_) \
+  case A_ * 8 + B_: issue_stage<A_, B_>(d0, adesc, bdesc, idesc_n, carry); break;
+  switch (pa * 8 + pb) {
+    QG_ISSUE(4, 4) QG_ISSUE(4, 2) QG_ISSUE(4, 1) QG_ISSUE(2, 4) QG_ISSUE(1, 4)
+    QG_ISSUE(2, 2) QG_ISSUE(2, 1) QG_ISSUE(1, 2)
+    default: issue_stage<1, 1>(d0, adesc, bdesc, idesc_n, carry); break;
+  }
+#undef QG_ISSUE
 }
 
 // Persistent split-BF16 GEMM.  Single problem: tensor maps and parameters
 // are kernel parameters, tiles rasterised in groups of kGroupM row tiles.
 // Grouped: tiles[t] = (problem, row tile, column tile), per-problem maps and
 // parameters in probs.  Err::word() is the device status word.
+// debug_skip > 0 makes the TMA warp leave out the copies of its running stage
+// debug_skip - 1 (fault injection for the bounded waits; 0 in normal use).
 template <class Err, bool GROUPED>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const GemmParams single, const SplitProb *__restrict__ probs,
-                const int4 *__restrict__ tiles, int ntiles, int chunk, uint64_t limit_ns) {
+                const int4 *__restrict__ tiles, int ntiles, uint64_t limit_ns, int debug_skip) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t raw_addr = smem_u32(smem_raw);
   unsigned char *ring = smem_raw + ((1024 - (raw_addr & 1023)) & 1023);
@@ -561,7 +782,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = ctl->tmem_base;
+  bool producer = false;  // the TMA thread, and the stages it issued
+  uint32_t issued = 0;
 
+  if (warp < 4) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsCtl));
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (elect_one()) {
@@ -579,6 +804,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (tile_skip(*g, mt, nt)) continue;
         int kb_lo, kb_hi;
         kb_range(*g, mt, nt, z, kb_lo, kb_hi);
+        const uint32_t bytes = static_cast<uint32_t>(g->pa) * TERMS * kAPlaneBytes +
+                               static_cast<uint32_t>(g->pb) * TERMS * kBPlaneBytes;
         for (int kb = kb_lo; kb < kb_hi; ++kb, ++s_run) {
           const int st = s_run % STAGES;
           if (!wait_phase(&ctl->empty[st], ((s_run / STAGES) & 1) ^ 1, limit_ns, ctl)) {
@@ -586,21 +813,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
+          if (debug_skip > 0 && s_run == static_cast<uint32_t>(debug_skip - 1)) continue;
           unsigned char *sa = ring + st * kStageBytes;
-          mbar_arrive_expect_tx(&ctl->full[st], kStageBytes);
-          tma_load_3d(sa, mA, &ctl->full[st], kb * BK, mt * BM, 0);
-          tma_load_3d(sa + kStageA, mB, &ctl->full[st], kb * BK, nt * BN, 0);
+          mbar_arrive_expect_tx(&ctl->full[st], bytes);
+          tma_load_4d(sa, mA, &ctl->full[st], kb * KQ, mt * BM, 0, 0);
+          tma_load_4d(sa + kStageA, mB, &ctl->full[st], kb * KQ, nt * BNQ, 0, 0);
         }
       }
-      if (!ok) {  // let this CTA's copies in flight land before it retires
-        for (uint32_t q = s_run > STAGES ? s_run - STAGES : 0; q < s_run; ++q)
-          mbar_wait_bounded(&ctl->full[q % STAGES], (q / STAGES) & 1, limit_ns);
-      }
+      producer = true;
+      issued = s_run;
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (elect_one()) {
-      constexpr uint32_t idesc = idesc_bf16(BM, BN);
       const uint32_t ring_addr = smem_u32(ring);
       uint32_t s_run = 0, c_run = 0;
       bool ok = true;
@@ -612,7 +837,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (tile_skip(*g, mt, nt)) continue;
         int kb_lo, nkb;
         kb_range(*g, mt, nt, z, kb_lo, nkb);
-        for (int kb = kb_lo; kb < nkb && ok; ++c_run) {
+        const uint32_t idesc = idesc_bf16(BM, tile_ncols(*g, nt));
+        const int pa = g->pa, pb = g->pb;
+        int ch = 0;
+        for (int kb = kb_lo; kb < nkb && ok; ++c_run, ++ch) {
           const int b = c_run & 1;
           if (!wait_phase(&ctl->accempty[b], ((c_run >> 1) & 1) ^ 1, limit_ns, ctl)) {
             set_abort<Err>(ctl);
@@ -620,9 +848,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t d = tmem + b * BN;
-          const int kb_end = min(nkb, kb + chunk);
-          bool first = true;
+          const uint32_t d = tmem + b * kBufCols;
+          const int kb_end = min(nkb, kb + kChunk);
+          bool carry = ch >= 2;
           for (; kb < kb_end; ++kb, ++s_run) {
             const int st = s_run % STAGES;
             if (!wait_phase(&ctl->full[st], (s_run / STAGES) & 1, limit_ns, ctl)) {
@@ -632,17 +860,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc_fence_after();
             const uint32_t sa = ring_addr + st * kStageBytes;
-            const uint32_t sb = sa + kStageA;
-#pragma unroll
-            for (int ks = 0; ks < BK / 16; ++ks) {
-#pragma unroll
-              for (int tp = 0; tp < 6; ++tp) {
-                const uint64_t ad = smem_desc_sw64(sa + term_a(tp) * kATermBytes + ks * 32);
-                const uint64_t bd = smem_desc_sw64(sb + term_b(tp) * kBTermBytes + ks * 32);
-                umma_bf16(d, ad, bd, idesc, first ? 0u : 1u);
-                first = false;
-              }
-            }
+            issue_stage_planes(pa, pb, d, smem_desc_sw32(sa), smem_desc_sw32(sa + kStageA),
+                               idesc, carry);
+            carry = true;  // later stages of the chunk add onto it
             umma_commit(&ctl->empty[st]);  // frees the stage when these MMAs finish
           }
           if (!ok) break;
@@ -653,11 +873,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       umma_commit(&ctl->done);
       mbar_wait_bounded(&ctl->done, 0, limit_ns);
     }
+  }
   } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsDrain));
     // ---------------- drain + epilogue (8 warps) ----------------
-    const int ew = warp - 2;
+    const int ew = warp - 4;
     const int quad = warp & 3;   // TMEM lanes 32*quad .. +31 (hardware rule: warp % 4)
-    const int half = ew >> 2;    // columns [128*half, 128*half + 128)
+    const int half = ew >> 2;    // quaternion columns [32*half, 32*half + 32) of the tile
     const uint32_t lane_base = static_cast<uint32_t>(32 * quad) << 16;
     uint32_t c_run = 0;
     bool ok = true;
@@ -669,8 +891,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (tile_skip(*g, mt, nt)) continue;
       int kb_lo, kb_hi;
       kb_range(*g, mt, nt, z, kb_lo, kb_hi);
-      const int nch = (kb_hi - kb_lo + chunk - 1) / chunk;
-      if (g->ksplit <= 1)
+      const int nch = (kb_hi - kb_lo + kChunk - 1) / kChunk;
+      const bool mine = 32 * half < tile_ncols(*g, nt);  // this warp's columns hold data
+      const int nacc = g->pa > g->pb ? g->pa : g->pb;    // components the MMAs write
+      if (g->ksplit <= 1 && mine)
         prefetch_c(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane,
                    static_cast<int64_t>(nt) * BNQ + 32 * half);
       float acc[128];
@@ -684,21 +908,39 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t base = tmem + lane_base + b * BN + half * 128;
-        // 32 columns per load: the drain warps' register budget is 168 per
-        // thread (10 warps per CTA, three on some SM sub-partitions)
+        // the rounding errors go back to TMEM when chunk ch + 2 of this tile
+        // accumulates onto them (same buffer)
+        const bool carry = ch + 2 < nch;
+        if (mine) {
+          const uint32_t base = tmem + lane_base + b * kBufCols + 32 * half;
+          // 16 columns at a time (the registers hold the 128 sums)
 #pragma unroll
-        for (int piece = 0; piece < 4; ++piece) {
-          float v[32];
-          tmem_ld32(base + piece * 32, v);
+          for (int pc = 0; pc < 2 * PLANES; ++pc) {
+            const int c = pc >> 1, h = 16 * (pc & 1);
+            float v[16];
+            tmem_ld16(base + c * BNQ + h, v);
+            // a component the MMAs do not write (narrow factors) adds zero
+            // (a select, not a branch: early exits here cost spills)
+            const bool live = c < nacc;
 #pragma unroll
-          for (int i = 0; i < 32; ++i) acc[piece * 32 + i] += v[i];
+            for (int q = 0; q < 16; ++q) v[q] = live ? v[q] : 0.f;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              float s, e;
+              two_sum(acc[32 * c + h + q], v[q], s, e);
+              acc[32 * c + h + q] = s;
+              v[q] = e;
+            }
+            if (carry) tmem_st16(base + c * BNQ + h, v);
+          }
+          if (carry) tmem_st_wait();
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&ctl->accempty[b]);
       }
       if (!ok) break;
+      if (!mine) continue;
       if (g->ksplit > 1)
         store_partial(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane,
                       static_cast<int64_t>(nt) * BNQ + 32 * half, z, acc);
@@ -710,415 +952,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   tc_fence_before();
   __syncthreads();
-  if (warp == 1) {
-    tc_fence_after();
-    tmem_dealloc(tmem, kTmemCols);
-  }
-}
-
-}  // namespace split
-}  // namespace qg
-
-namespace qg {
-namespace split {
-
-// --------------------------------------------------------- fused path ---
-// The same product without a workspace: FP32 tiles of op(A) and op(B) come in
-// by TMA in their stored layout (3-D boxes as in the FP64 path, zero fill past
-// the edges), two converter warps split them into the three BF16 terms and
-// write A' and the sign-expanded B' directly into the 64-byte-swizzled
-// K-major layout of the MMA operands, then hand the stage to the MMA warp
-// (generic-proxy writes made visible to the tensor core by
-// fence.proxy.async).  Used where the operand pre-pass would cost more HBM
-// traffic than it saves (many small problems).
-constexpr int FSTAGES = 2;                          // BF16 operand stages
-constexpr int FSTAGING = 3;                         // FP32 staging slots
-constexpr int kConvWarps = 2;
-constexpr int kFusedThreads = kThreads + 32 * kConvWarps;
-constexpr int FKQ = BK / 4;                         // quaternion k per stage (8)
-constexpr uint32_t kStagingA = BM * FKQ * 16;       // 16 KB FP32 op(A) tile
-constexpr uint32_t kStagingB = BNQ * FKQ * 16;      // 8 KB FP32 op(B) tile
-constexpr uint32_t kStagingBytes = kStagingA + kStagingB;
-constexpr size_t kFusedSmemBytes =
-    1024 + FSTAGES * kStageBytes + FSTAGING * kStagingBytes + 256;
-
-// Per-problem parameters of the fused path.
-struct FusedOps {
-  int layout;
-  int ta, tb;          // op(A) / op(B) transposed (T or H)
-  uint32_t conj_a;     // component sign masks (bit s: negate component s)
-  uint32_t conj_b;
-};
-
-struct alignas(128) FusedProb {
-  CUtensorMap tmA;     // FP32 stored A, 3-D box
-  CUtensorMap tmB;     // FP32 stored B, 3-D box
-  FusedOps o;
-  GemmParams g;
-};
-
-struct FusedCtl {
-  uint64_t sfull[FSTAGING];   // FP32 staging landed (TMA)
-  uint64_t sempty[FSTAGING];  // FP32 staging consumed (converters)
-  uint64_t full[FSTAGES];     // BF16 stage written (converters)
-  uint64_t empty[FSTAGES];    // BF16 stage consumed (MMA commit)
-  uint64_t accfull[2];
-  uint64_t accempty[2];
-  uint64_t done;
-  uint32_t tmem_base;
-  int abort;
-};
-
-// Byte offset of element (row, k) (k < 32 bf16) in a K-major tile with
-// 64-byte rows and the 64-byte swizzle (16-byte chunk index XOR bits 1..2 of
-// the row), the layout TMA writes with CU_TENSOR_MAP_SWIZZLE_64B.
-__device__ __forceinline__ uint32_t sw64_offset(int row, int k) {
-  const int chunk = (k >> 3) ^ ((row >> 1) & 3);
-  return static_cast<uint32_t>(row * 64 + chunk * 16 + (k & 7) * 2);
-}
-
-// Index (in floats) of component s of op-tile element (r, kk) in the FP32
-// staging tile.  The TMA box order is the stored order: for the stored
-// element (sr, sc) of a box with R stored rows and CC stored columns,
-// interleaved: s + 4 (sr + R sc);  planes: sr + R (sc + CC s).
-__device__ __forceinline__ int staging_idx(int layout, bool trans, int R_op, int r, int kk,
-                                           int s) {
-  // op-tile is R_op rows x FKQ k; stored tile is (R_op x FKQ) or transposed
-  const int sr = trans ? kk : r, sc = trans ? r : kk;
-  const int R = trans ? FKQ : R_op, CC = trans ? R_op : FKQ;
-  if (layout == QGEMM_INTERLEAVED) return s + 4 * (sr + R * sc);
-  return sr + R * (sc + CC * s);
-}
-
-__device__ __forceinline__ void store_bf16x4(unsigned char *tile, int row, int k0,
-                                             __nv_bfloat16 a, __nv_bfloat16 b,
-                                             __nv_bfloat16 c, __nv_bfloat16 d) {
-  __align__(8) __nv_bfloat16 w[4] = {a, b, c, d};
-  *reinterpret_cast<uint2 *>(tile + sw64_offset(row, k0)) = *reinterpret_cast<const uint2 *>(w);
-}
-
-// Converter: FP32 staging slot -> BF16 stage (A' rows i, B' rows 4n + c).
-__device__ __forceinline__ void convert_stage(const float *stA, const float *stB,
-                                              unsigned char *stage, const FusedOps &o,
-                                              int ctid) {
-  // A': 128 rows x 8 quaternion k; thread handles (row, kk) pairs
-  for (int e = ctid; e < BM * FKQ; e += 32 * kConvWarps) {
-    const int r = e % BM, kk = e / BM;
-    float v[4];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      v[s] = stA[staging_idx(o.layout, o.ta, BM, r, kk, s)];
-      if ((o.conj_a >> s) & 1u) v[s] = -v[s];
-    }
-    Split3 sp[4];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) sp[s] = split3(v[s]);
-#pragma unroll
-    for (int t = 0; t < TERMS; ++t)
-      store_bf16x4(stage + t * kATermBytes, r, 4 * kk, sp[0].t[t], sp[1].t[t], sp[2].t[t],
-                   sp[3].t[t]);
-  }
-  // B': 64 quaternion columns x 8 quaternion k -> rows 4n + c
-  unsigned char *sb = stage + kStageA;
-  for (int e = ctid; e < BNQ * FKQ; e += 32 * kConvWarps) {
-    const int n = e % BNQ, kk = e / BNQ;
-    float v[4];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      // op(B) tile element (kk, n): use the op-row = n convention of staging_idx
-      v[s] = stB[o.tb ? staging_idx(o.layout, false, BNQ, n, kk, s)
-                      : staging_idx(o.layout, true, BNQ, n, kk, s)];
-      if ((o.conj_b >> s) & 1u) v[s] = -v[s];
-    }
-    Split3 sp[4];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) sp[s] = split3(v[s]);
-#pragma unroll
-    for (int t = 0; t < TERMS; ++t)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        __nv_bfloat16 w[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int q = j ^ c;
-          w[j] = basis_sign(j, q) < 0 ? __hneg(sp[q].t[t]) : sp[q].t[t];
-        }
-        store_bf16x4(sb + t * kBTermBytes, 4 * n + c, 4 * kk, w[0], w[1], w[2], w[3]);
-      }
-  }
-}
-
-__device__ __forceinline__ void tma_stage(float *dst, const CUtensorMap *map, uint64_t *bar,
-                                          int layout, int r0, int c0) {
-  if (layout == QGEMM_INTERLEAVED)
-    tma_load_3d(dst, map, bar, 0, r0, c0);
-  else
-    tma_load_3d(dst, map, bar, r0, c0, 0);
-}
-
-template <bool GROUPED>
-__device__ __forceinline__ void fused_tile_of(int t, const GemmParams &single,
-                                              const FusedOps &single_o, const CUtensorMap *smA,
-                                              const CUtensorMap *smB, const FusedProb *probs,
-                                              const int4 *tiles, const GemmParams *&g,
-                                              const FusedOps *&o, const CUtensorMap *&mA,
-                                              const CUtensorMap *&mB, int &mt, int &nt) {
-  if (GROUPED) {
-    const int4 e = tiles[t];
-    const FusedProb *pr = probs + e.x;
-    g = &pr->g;
-    o = &pr->o;
-    mA = &pr->tmA;
-    mB = &pr->tmB;
-    mt = e.y;
-    nt = e.z;
-  } else {
-    g = &single;
-    o = &single_o;
-    mA = smA;
-    mB = smB;
-    const int per_group = kGroupM * single.num_nt;
-    const int first_m = (t / per_group) * kGroupM;
-    const int gsize = min(single.num_mt - first_m, kGroupM);
-    mt = first_m + (t % per_group) % gsize;
-    nt = (t % per_group) / gsize;
-    // a triangular operand: the tiles with the longest k-range first, so the
-    // CTAs' round-robin shares stay balanced
-    if (single.krange == 1) mt = single.num_mt - 1 - mt;
-    if (single.krange == 4) nt = single.num_nt - 1 - nt;
-  }
-}
-
-template <class Err>
-__device__ __forceinline__ void fused_abort(FusedCtl *ctl) {
-  atomicCAS(Err::word(), 0, QGEMM_ERR_TIMEOUT);
-  *reinterpret_cast<volatile int *>(&ctl->abort) = 1;
-}
-__device__ __forceinline__ bool fused_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
-                                           FusedCtl *ctl) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = globaltimer_ns();
-  while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (*reinterpret_cast<volatile int *>(&ctl->abort) != 0 || globaltimer_ns() - t0 > limit_ns)
-      return false;
-  }
-}
-
-// Warps: 0 TMA (FP32 staging), 1 MMA, 2..9 drain + epilogue, 10..11 convert.
-template <class Err, bool GROUPED>
-__global__ void __launch_bounds__(kFusedThreads, 1)
-    fused_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                 const GemmParams single, const FusedOps single_o,
-                 const FusedProb *__restrict__ probs, const int4 *__restrict__ tiles, int ntiles,
-                 int chunk, uint64_t limit_ns) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  const uint32_t raw_addr = smem_u32(smem_raw);
-  unsigned char *ring = smem_raw + ((1024 - (raw_addr & 1023)) & 1023);
-  float *staging = reinterpret_cast<float *>(ring + FSTAGES * kStageBytes);
-  FusedCtl *ctl = reinterpret_cast<FusedCtl *>(reinterpret_cast<unsigned char *>(staging) +
-                                               FSTAGING * kStagingBytes);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < FSTAGING; ++s) {
-      mbar_init(&ctl->sfull[s], 1);
-      mbar_init(&ctl->sempty[s], kConvWarps);
-    }
-    for (int s = 0; s < FSTAGES; ++s) {
-      mbar_init(&ctl->full[s], kConvWarps);
-      mbar_init(&ctl->empty[s], 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&ctl->accfull[b], 1);
-      mbar_init(&ctl->accempty[b], kEpiWarps);
-    }
-    mbar_init(&ctl->done, 1);
-    ctl->abort = 0;
-    fence_barrier_init();
-  }
-  if (warp == 1) tmem_alloc(&ctl->tmem_base, kTmemCols);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = ctl->tmem_base;
-
-  if (warp == 0) {
-    // ---------------- TMA producer: FP32 tiles ----------------
-    if (elect_one()) {
-      uint32_t s_run = 0;
-      bool ok = true;
-      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const GemmParams *g;
-        const FusedOps *o;
-        const CUtensorMap *mA, *mB;
-        int mt, nt;
-        fused_tile_of<GROUPED>(t, single, single_o, &tmA, &tmB, probs, tiles, g, o, mA, mB, mt,
-                               nt);
-        if (tile_skip(*g, mt, nt)) continue;
-        const int nkb = g->num_kb;
-        const int layout = o->layout, ta = o->ta, tb = o->tb;
-        for (int kb = 0; kb < nkb; ++kb, ++s_run) {
-          const int st = s_run % FSTAGING;
-          if (!fused_wait(&ctl->sempty[st], ((s_run / FSTAGING) & 1) ^ 1, limit_ns, ctl)) {
-            fused_abort<Err>(ctl);
-            ok = false;
-            break;
-          }
-          float *sa = staging + st * (kStagingBytes / 4);
-          float *sb = sa + kStagingA / 4;
-          mbar_arrive_expect_tx(&ctl->sfull[st], kStagingBytes);
-          const int k0 = kb * FKQ;
-          tma_stage(sa, mA, &ctl->sfull[st], layout, ta ? k0 : mt * BM, ta ? mt * BM : k0);
-          tma_stage(sb, mB, &ctl->sfull[st], layout, tb ? nt * BNQ : k0, tb ? k0 : nt * BNQ);
-        }
-      }
-      if (!ok) {
-        for (uint32_t q = s_run > FSTAGING ? s_run - FSTAGING : 0; q < s_run; ++q)
-          mbar_wait_bounded(&ctl->sfull[q % FSTAGING], (q / FSTAGING) & 1, limit_ns);
-      }
-    }
-  } else if (warp >= 2 + kEpiWarps) {
-    // ---------------- converters ----------------
-    const int ctid = threadIdx.x - 32 * (2 + kEpiWarps);
-    uint32_t s_run = 0, b_run = 0;
-    bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const GemmParams *g;
-      const FusedOps *o;
-      const CUtensorMap *mA, *mB;
-      int mt, nt;
-      fused_tile_of<GROUPED>(t, single, single_o, &tmA, &tmB, probs, tiles, g, o, mA, mB, mt,
-                             nt);
-      if (tile_skip(*g, mt, nt)) continue;
-      const FusedOps ops = *o;
-      const int nkb = g->num_kb;
-      for (int kb = 0; kb < nkb; ++kb, ++s_run, ++b_run) {
-        const int ss = s_run % FSTAGING, bs = b_run % FSTAGES;
-        if (!fused_wait(&ctl->sfull[ss], (s_run / FSTAGING) & 1, limit_ns, ctl) ||
-            !fused_wait(&ctl->empty[bs], ((b_run / FSTAGES) & 1) ^ 1, limit_ns, ctl)) {
-          fused_abort<Err>(ctl);
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const float *sa = staging + ss * (kStagingBytes / 4);
-        convert_stage(sa, sa + kStagingA / 4, ring + bs * kStageBytes, ops, ctid);
-        fence_proxy_async_smem();  // the tensor core reads what the threads wrote
-        __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&ctl->sempty[ss]);
-          mbar_arrive(&ctl->full[bs]);
-        }
-      }
-    }
-  } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------
-    if (elect_one()) {
-      constexpr uint32_t idesc = idesc_bf16(BM, BN);
-      const uint32_t ring_addr = smem_u32(ring);
-      uint32_t b_run = 0, c_run = 0;
-      bool ok = true;
-      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const GemmParams *g;
-        const FusedOps *o;
-        const CUtensorMap *mA, *mB;
-        int mt, nt;
-        fused_tile_of<GROUPED>(t, single, single_o, &tmA, &tmB, probs, tiles, g, o, mA, mB, mt,
-                               nt);
-        if (tile_skip(*g, mt, nt)) continue;
-        const int nkb = g->num_kb;  // the fused path runs all of K
-        for (int kb = 0; kb < nkb && ok; ++c_run) {
-          const int b = c_run & 1;
-          if (!fused_wait(&ctl->accempty[b], ((c_run >> 1) & 1) ^ 1, limit_ns, ctl)) {
-            fused_abort<Err>(ctl);
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t d = tmem + b * BN;
-          const int kb_end = min(nkb, kb + chunk);
-          bool first = true;
-          for (; kb < kb_end; ++kb, ++b_run) {
-            const int st = b_run % FSTAGES;
-            if (!fused_wait(&ctl->full[st], (b_run / FSTAGES) & 1, limit_ns, ctl)) {
-              fused_abort<Err>(ctl);
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-            const uint32_t sa = ring_addr + st * kStageBytes;
-            const uint32_t sb = sa + kStageA;
-#pragma unroll
-            for (int ks = 0; ks < BK / 16; ++ks) {
-#pragma unroll
-              for (int tp = 0; tp < 6; ++tp) {
-                const uint64_t ad = smem_desc_sw64(sa + term_a(tp) * kATermBytes + ks * 32);
-                const uint64_t bd = smem_desc_sw64(sb + term_b(tp) * kBTermBytes + ks * 32);
-                umma_bf16(d, ad, bd, idesc, first ? 0u : 1u);
-                first = false;
-              }
-            }
-            umma_commit(&ctl->empty[st]);
-          }
-          if (!ok) break;
-          umma_commit(&ctl->accfull[b]);
-        }
-      }
-      umma_commit(&ctl->done);
-      mbar_wait_bounded(&ctl->done, 0, limit_ns);
-    }
-  } else {
-    // ---------------- drain + epilogue (8 warps) ----------------
-    const int ew = warp - 2;
-    const int quad = warp & 3;
-    const int half = ew >> 2;
-    const uint32_t lane_base = static_cast<uint32_t>(32 * quad) << 16;
-    uint32_t c_run = 0;
-    bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const GemmParams *g;
-      const FusedOps *o;
-      const CUtensorMap *mA, *mB;
-      int mt, nt;
-      fused_tile_of<GROUPED>(t, single, single_o, &tmA, &tmB, probs, tiles, g, o, mA, mB, mt,
-                             nt);
-      if (tile_skip(*g, mt, nt)) continue;
-      const int nkb = g->num_kb;
-      const int nch = (nkb + chunk - 1) / chunk;
-      prefetch_c(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane,
-                 static_cast<int64_t>(nt) * BNQ + 32 * half);
-      float acc[128];
-#pragma unroll
-      for (int i = 0; i < 128; ++i) acc[i] = 0.f;
-      for (int ch = 0; ch < nch; ++ch, ++c_run) {
-        const int b = c_run & 1;
-        if (!fused_wait(&ctl->accfull[b], (c_run >> 1) & 1, limit_ns, ctl)) {
-          fused_abort<Err>(ctl);
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t base = tmem + lane_base + b * BN + half * 128;
-#pragma unroll
-        for (int piece = 0; piece < 4; ++piece) {
-          float v[32];
-          tmem_ld32(base + piece * 32, v);
-#pragma unroll
-          for (int i = 0; i < 32; ++i) acc[piece * 32 + i] += v[i];
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&ctl->accempty[b]);
-      }
-      if (!ok) break;
-      epilogue(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane,
-               static_cast<int64_t>(nt) * BNQ + 32 * half, acc);
+  if (producer && aborted(ctl)) {
+    // copies the MMA warp never waited for land before the CTA retires
+    for (uint32_t q = issued > STAGES ? issued - STAGES : 0; q < issued; ++q) {
+      if (debug_skip > 0 && q == static_cast<uint32_t>(debug_skip - 1)) continue;
+      mbar_wait_bounded(&ctl->full[q % STAGES], (q / STAGES) & 1, limit_ns);
     }
   }
-
-  tc_fence_before();
-  __syncthreads();
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem, kTmemCols);

@@ -44,22 +44,33 @@ def precision_of(dtype, precision=None):
     raise ValueError("precision %r does not take %s data" % (precision, dtype))
 
 
-def workspace(nbytes, device):
-    """A cached device workspace of at least nbytes (grown on demand)."""
-    if nbytes == 0:
-        return None
-    key = torch.device(device).index or 0
-    ws = _workspaces.get(key)
-    if ws is None or ws.numel() < nbytes:
-        ws = torch.empty(max(nbytes, 1 << 20), dtype=torch.uint8, device=device)
-        _workspaces[key] = ws
-    return ws
+def _stream_of(stream, device=None):
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return stream
 
 
 def _stream_handle(stream):
-    if stream is None:
-        stream = torch.cuda.current_stream()
-    return stream.cuda_stream
+    return _stream_of(stream).cuda_stream
+
+
+def workspace(nbytes, device, stream=None):
+    """A cached device workspace of at least nbytes for calls on `stream`
+    (torch's current stream when None), grown on demand.  Each (device,
+    stream) pair has its own buffer, allocated on that stream, so calls on
+    unordered streams never share a workspace, and a buffer replaced by a
+    larger one goes back to torch's allocator on the stream that used it."""
+    if nbytes == 0:
+        return None
+    dev = torch.device(device)
+    s = _stream_of(stream, dev)
+    key = (dev.index or 0, s.cuda_stream)
+    ws = _workspaces.get(key)
+    if ws is None or ws.numel() < nbytes:
+        with torch.cuda.stream(s):
+            ws = torch.empty(max(nbytes, 1 << 20), dtype=torch.uint8, device=dev)
+        _workspaces[key] = ws
+    return ws
 
 
 def qgemm(opA, opB, m, n, k, alpha, A, B, beta, C, layout="interleaved", ws=None,
@@ -81,7 +92,7 @@ def qgemm(opA, opB, m, n, k, alpha, A, B, beta, C, layout="interleaved", ws=None
     need = L.qgemm_workspace_bytes(_abi.OP[opA], _abi.OP[opB], m, n, k, _abi.LAYOUT[layout],
                                    _abi.PRECISION[prec])
     if ws is None:
-        ws = workspace(need, C.device)
+        ws = workspace(need, C.device, stream)
     wptr = ws.data_ptr() if ws is not None else None
     wbytes = ws.numel() * ws.element_size() if ws is not None else 0
     rc = L.qgemm(_abi.OP[opA], _abi.OP[opB], m, n, k, _abi.q4(alpha), A.data_ptr(), lda, psA,
@@ -102,7 +113,7 @@ def qherk(uplo, trans, n, k, alpha, A, beta, C, layout="interleaved", ws=None, s
     up, tr = {"L": 0, "U": 1}[uplo], _abi.OP[trans]
     need = L.qherk_workspace_bytes(up, tr, n, k, _abi.LAYOUT[layout], _abi.PRECISION[prec])
     if ws is None:
-        ws = workspace(need, C.device)
+        ws = workspace(need, C.device, stream)
     wptr = ws.data_ptr() if ws is not None else None
     wbytes = ws.numel() * ws.element_size() if ws is not None else 0
     rc = L.qherk(up, tr, n, k, float(alpha), A.data_ptr(), lda, psA, float(beta), C.data_ptr(),
@@ -148,7 +159,7 @@ def qgemm_mixed(typeA, typeB, opA, opB, m, n, k, alpha, A, B, beta, C, layout="i
     head = (_TYPE[typeA], _TYPE[typeB], _abi.OP[opA], _abi.OP[opB], m, n, k)
     need = L.qgemm_mixed_workspace_bytes(*head, _abi.LAYOUT[layout], _abi.PRECISION[prec])
     if ws is None:
-        ws = workspace(need, C.device)
+        ws = workspace(need, C.device, stream)
     wptr = ws.data_ptr() if ws is not None else None
     wbytes = ws.numel() * ws.element_size() if ws is not None else 0
     rc = L.qgemm_mixed(*head, _abi.q4(alpha), A.data_ptr(), lda, psA, B.data_ptr(), ldb, psB,
@@ -174,7 +185,7 @@ def qtrmm(side, uplo, trans, diag, m, n, alpha, A, B, C, layout="interleaved", w
             {"N": 0, "U": 1}[diag], m, n)
     need = L.qtrmm_workspace_bytes(*args, _abi.LAYOUT[layout], _abi.PRECISION[prec])
     if ws is None:
-        ws = workspace(need, C.device)
+        ws = workspace(need, C.device, stream)
     wptr = ws.data_ptr() if ws is not None else None
     wbytes = ws.numel() * ws.element_size() if ws is not None else 0
     rc = L.qtrmm(*args, _abi.q4(alpha), A.data_ptr(), lda, psA, B.data_ptr(), ldb, psB,
@@ -196,7 +207,7 @@ def qgemm_backward(X, W, dY, mb, k, n, dX=None, dW=None, accumulate=False,
     lddw, psdw = (geometry(dW, layout)[:2] if dW is not None else (max(k, 1), 0))
     need = L.qgemm_backward_workspace_bytes(mb, k, n, _abi.LAYOUT[layout], _abi.PRECISION[prec])
     if ws is None:
-        ws = workspace(need, X.device)
+        ws = workspace(need, X.device, stream)
     wptr = ws.data_ptr() if ws is not None else None
     wbytes = ws.numel() * ws.element_size() if ws is not None else 0
     rc = L.qgemm_backward(mb, k, n, X.data_ptr(), ldx, psx, W.data_ptr(), ldw, psw,

@@ -172,10 +172,11 @@ def test_fp64_split_k_workspace():
                  C=64) in (0, _abi.ERR_NO_DEVICE)
 
 
-def _tc_shares(m, n, k, bm, bnq, min_kb, sms=152):
+def _tc_shares(m, n, k, bm, bnq, min_kb, sms=152, kb_quat=8):
     """K shares of a tensor-core path: tiles of bm x bnq quaternions, one
-    CTA per SM, k-blocks of 32 reals, at least min_kb per share; split only
-    when at most half the SMs are busy unsplit."""
+    CTA per SM, k-blocks of kb_quat quaternion k (8: 32 reals), at least
+    min_kb per share; split only when at most half the SMs are busy
+    unsplit."""
     tiles = -(-m // bm) * -(-n // bnq)
     if tiles >= 8 * sms:
         return 1
@@ -184,7 +185,7 @@ def _tc_shares(m, n, k, bm, bnq, min_kb, sms=152):
         return tiles * s / (-(-tiles * s // sms) * sms)
     if busy(1) > 0.5:
         return 1
-    shares = range(2, min(256, (-(-4 * k // 32)) // min_kb) + 1)
+    shares = range(2, min(256, (-(-k // kb_quat)) // min_kb) + 1)
     top = max([busy(1)] + [busy(s) for s in shares])
     if top < busy(1) + 0.05:
         return 1
@@ -195,13 +196,16 @@ def test_tensor_core_split_k_workspace():
     """Split-BF16 and digit-sliced paths: beyond the required operand
     workspace, qgemm_workspace_bytes reports s partial products (16 bytes
     per quaternion for the FP32 split path after the required part rounded
-    to 256 bytes, 32 bytes for the FP64 digit-sliced path)."""
+    to 256 bytes, 32 bytes for the FP64 digit-sliced path).  The split path's
+    operands are 3 BF16 terms x 4 component planes of each factor, kappa
+    pitch rounded up to 8; its shares count stages of 16 quaternion k, at
+    least 32 per share."""
     L = _abi.lib()
     for (m, n, k) in ((64, 64, 65536), (37, 29, 8000), (200, 130, 6000), (1024, 1024, 8192)):
-        kp = -(-4 * k // 32) * 32
-        a_bytes = 3 * m * kp * 2
+        kp = -(-k // 8) * 8
+        a_bytes = 3 * 4 * m * kp * 2
         req = -(-a_bytes // 1024) * 1024 + 3 * 4 * n * kp * 2
-        ks = _tc_shares(m, n, k, 128, 64, 64)
+        ks = _tc_shares(m, n, k, 128, 64, 32, kb_quat=16)
         want = req if ks == 1 else -(-req // 256) * 256 + ks * m * n * 16
         assert L.qgemm_workspace_bytes(0, 0, m, n, k, 0, 1) == want, (m, n, k)
     for (m, n, k) in ((64, 64, 20000), (37, 29, 3000), (130, 70, 4000), (1024, 1024, 4096)):
@@ -211,8 +215,8 @@ def test_tensor_core_split_k_workspace():
         ks = _tc_shares(m, n, k, 128, 16, 32)
         extra = ks * m * n * 32 if ks > 1 else 0
         assert slices <= got - extra <= slices + 12 * (m + n) + 8 * 1024, (m, n, k)
-    assert _tc_shares(1024, 1024, 8192, 128, 64, 64) == 1   # 128 tiles: not split
-    assert _tc_shares(64, 64, 65536, 128, 64, 64) > 1
+    assert _tc_shares(1024, 1024, 8192, 128, 64, 32, kb_quat=16) == 1   # 128 tiles: not split
+    assert _tc_shares(64, 64, 65536, 128, 64, 32, kb_quat=16) > 1
 
 
 def test_sliced_precision_workspace():

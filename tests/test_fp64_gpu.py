@@ -144,6 +144,24 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     check("N", "N", 16, 16, 16, "interleaved", 77)                  # still usable
 
 
+@pytest.mark.parametrize("stage", [0, 2])
+def test_gemm_abort_path_reports_timeout_and_context_survives(stage):
+    """A fault armed in the FP64 GEMM: the TMA producer of the first CTA
+    leaves out the copies of one ring stage, so the consumers' bounded wait
+    (20 ms) gives up.  The CTA drains its own copies in flight and stops; the
+    launch reports QGEMM_ERR_TIMEOUT through the device status word and the
+    next call on the same context computes the right product."""
+    L = _abi.lib()
+    assert L.qgemm_get_last_device_error() == 0
+    m, n, k = 32, 32, 64                      # one CTA, four k-blocks
+    A, B, C = make_case("N", "N", m, n, k, "interleaved", 81)
+    assert L.qgemm_debug_arm_fault(0, stage, 20_000_000) == 0
+    gpu_run("N", "N", m, n, k, ALPHA, A, B, BETA, C, "interleaved")  # launch succeeds
+    assert L.qgemm_get_last_device_error() == _abi.ERR_TIMEOUT
+    assert L.qgemm_get_last_device_error() == 0
+    check("N", "N", m, n, k, "interleaved", 81)
+
+
 def _sampled_check(opA, opB, n, layout, seed, nrand=384):
     """m = n = k = n: sampled entries (2 full rows, 2 full columns, random
     entries) by exact oracle dot products, plus 2 Freivalds probes."""

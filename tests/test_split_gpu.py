@@ -121,48 +121,48 @@ def test_sampled_8192(kind):
     assert err <= TOL
 
 
+SCALARS = {
+    "one": np.array([1.0, 0.0, 0.0, 0.0]),
+    "real": np.array([-1.75, 0.0, 0.0, 0.0]),
+    "complex": np.array([0.5, -1.25, 0.0, 0.0]),
+    "quaternion": np.array([0.5, -1.0, 2.0, 0.25]),
+    "zero": np.zeros(4),
+}
+
+
 @pytest.mark.parametrize("layout", qsynth.LAYOUTS)
-@pytest.mark.parametrize("opA,opB", [("N", "N"), ("T", "H"), ("C", "T"), ("H", "C")])
-def test_fused_single_problem_path(opA, opB, layout, monkeypatch):
-    """The single-problem fused path (no workspace; operands converted in
-    shared memory) on ragged shapes; planes need ld % 4 == 0 for TMA."""
-    monkeypatch.setenv("QGEMM_SPLIT_FUSED", "1")
-    m, n, k = 150, 70, 45
-    A, B, C = make_case(opA, opB, m, n, k, layout, 1200 + OPS.index(opA), dtype=np.float32,
-                        pad=(4 - qsynth.stored_shape(opA, m, k)[0] % 4 if layout == "planes" else 1,
-                             4 - qsynth.stored_shape(opB, k, n)[0] % 4 if layout == "planes" else 1,
-                             2 if layout == "planes" else 3))
-    ref = oracle_full(opA, opB, m, n, k, ALPHA, A, B, BETA, C, layout)
-    dA, dB, dC = (to_dev(X, torch.float32) for X in (A, B, C))
-    lda, psA, _ = ops.geometry(dA, layout)
-    ldb, psB, _ = ops.geometry(dB, layout)
-    ldc, psC, _ = ops.geometry(dC, layout)
-    # the pointer-less query stays conservative; the call itself needs no workspace
-    rc = _abi.lib().qgemm(OPS.index(opA), OPS.index(opB), m, n, k, _abi.q4(ALPHA), dA.data_ptr(),
-                          lda, psA, dB.data_ptr(), ldb, psB, _abi.q4(BETA), dC.data_ptr(), ldc,
-                          psC, qsynth.LAYOUTS.index(layout), 1, None, 0,
-                          torch.cuda.current_stream().cuda_stream)
-    assert rc == 0
-    torch.cuda.synchronize()
-    got = dC.double().cpu().numpy()
-    assert rel_fro(qsynth.components(got, m, layout), qsynth.components(ref, m, layout)) <= TOL
-    assert np.all(np.isnan(padding(got, m, layout)))
+@pytest.mark.parametrize("alpha", ["one", "real", "complex", "quaternion"])
+@pytest.mark.parametrize("beta", ["zero", "real", "quaternion"])
+def test_scalar_kinds(alpha, beta, layout):
+    """alpha is applied to op(A) by the pre-pass (not at all when it is 1,
+    componentwise when real, as a left Hamilton product otherwise) and beta
+    C by the epilogue (skipped, real or quaternion): every combination on a
+    ragged shape with conjugated operands against the oracle."""
+    check("C", "T", 150, 70, 45, layout, seed=1200 + len(alpha) + 7 * len(beta),
+          alpha=SCALARS[alpha], beta=SCALARS[beta])
+
+
+@pytest.mark.parametrize("ncols", [1, 15, 16, 17, 33, 48, 63, 64, 65, 80])
+def test_column_tile_widths(ncols):
+    """The MMA width follows the last column tile (16-column granules up to
+    64): every width on both sides of a granule edge."""
+    check("N", "N", 130, ncols, 40, "interleaved", seed=1300 + ncols)
 
 
 # ---------------------------------------------------------------- K split ---
 def split_shares(m, n, k, sms):
     """Shares the split-BF16 path splits a single product into (tiles of 128
-    x 64 quaternions, one CTA per SM, >= 64 k-blocks of 32 reals each)."""
+    x 64 quaternions, one CTA per SM, >= 32 stages of 16 quaternion k)."""
     tiles = -(-m // 128) * -(-n // 64)
     if tiles >= 8 * sms:
         return 1
-    num_kb = -(-4 * k // 32)
+    num_kb = -(-k // 16)
 
     def busy(s):
         return tiles * s / (-(-tiles * s // sms) * sms)
     if busy(1) > 0.5:                # at most half of the SMs busy unsplit
         return 1
-    shares = range(2, min(256, num_kb // 64) + 1)
+    shares = range(2, min(256, num_kb // 32) + 1)
     top = max([busy(1)] + [busy(s) for s in shares])
     if top < busy(1) + 0.05:
         return 1
@@ -239,3 +239,60 @@ def test_split_k_optional_part_and_speed():
     for out in outs:                 # each within the bar of the exact product
         assert rel_fro(out, ref) <= TOL
     assert times[0] * 3 < times[1]
+
+
+def test_two_unordered_streams_use_separate_workspaces():
+    """Two qgemm calls on two streams with no ordering between them: each
+    stream gets its own cached workspace, so both results equal the same
+    products computed one after the other on one stream."""
+    m, n, k = 300, 200, 700
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(91)
+    A = [torch.randn((k, m, 4), dtype=torch.float32, device="cuda", generator=gen)
+         for _ in range(2)]
+    B = [torch.randn((n, k, 4), dtype=torch.float32, device="cuda", generator=gen)
+         for _ in range(2)]
+    C0 = torch.randn((n, m, 4), dtype=torch.float32, device="cuda", generator=gen)
+    ref = [C0.clone() for _ in range(2)]
+    for i in range(2):
+        ops.qgemm("N", "N", m, n, k, ALPHA, A[i], B[i], BETA, ref[i])
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    out = [C0.clone() for _ in range(2)]
+    torch.cuda.synchronize()
+    for rep in range(3):
+        for i in range(2):
+            out[i].copy_(C0)
+        torch.cuda.synchronize()
+        for i in range(2):
+            with torch.cuda.stream(streams[i]):
+                ops.qgemm("N", "N", m, n, k, ALPHA, A[i], B[i], BETA, out[i])
+        torch.cuda.synchronize()
+        for i in range(2):
+            assert torch.equal(out[i], ref[i]), "stream %d, repetition %d" % (i, rep)
+
+
+@pytest.mark.parametrize("stage", [0, 3])
+def test_gemm_abort_path_reports_timeout_and_context_survives(stage):
+    """A fault armed in the split-BF16 GEMM: its TMA warp leaves out the
+    copies of one ring stage, so the MMA warp's bounded wait (20 ms) gives
+    up.  Every role of the CTA stops (the abort flag ends the other waits),
+    the copies in flight land, all issued MMAs complete, tensor memory is
+    released, and the launch reports QGEMM_ERR_TIMEOUT; the next call on the
+    same context computes the right product."""
+    L = _abi.lib()
+    assert L.qgemm_get_last_device_error() == 0
+    m, n, k = 100, 40, 80                      # one tile, five 16-kappa stages
+    A, B, C = make_case("N", "N", m, n, k, "interleaved", 82, dtype=np.float32)
+    assert L.qgemm_debug_arm_fault(1, stage, 20_000_000) == 0
+    gpu_run("N", "N", m, n, k, ALPHA, A, B, BETA, C, "interleaved", dtype=torch.float32)
+    assert L.qgemm_get_last_device_error() == _abi.ERR_TIMEOUT
+    assert L.qgemm_get_last_device_error() == 0
+    check("N", "N", m, n, k, "interleaved", 82)
+
+
+def test_arm_fault_argument_checks():
+    L = _abi.lib()
+    assert L.qgemm_debug_arm_fault(2, 0, 20_000_000) == -1
+    assert L.qgemm_debug_arm_fault(1, -1, 20_000_000) == -2
+    assert L.qgemm_debug_arm_fault(1, 0, 10) == -3

@@ -1,8 +1,8 @@
 """The fixed-scratch split-BF16 entry point, qgemm_split_noalloc.
 
-It exists for callers that cannot allocate device memory at the call (code
-running under CUDA-graph capture, memory owned by another allocator, plain C
-callers without an allocator).  It must give the same result as qgemm() with
+It exists for callers that cannot allocate device memory at the call: code
+whose device memory all belongs to another allocator (a framework's pool, a
+fixed arena), or a plain C caller that has no allocator of its own.  It must give the same result as qgemm() with
 a caller workspace.  This file sorts last so that a run stopping at the first
 failure has run everything else; it also passes alone in a fresh process."""
 import numpy as np
@@ -31,7 +31,10 @@ def _noalloc(opA, opB, m, n, k, alpha, A, B, beta, C, layout):
 def test_noalloc_matches_workspace_entry_point_twice(layout):
     """Two calls in a row (different shapes, so stale scratch contents from the
     first call would show in the second), each against qgemm()."""
-    cases = [("N", "H", 300, 260, 200, 11), ("T", "N", 130, 70, 45, 12)]
+    cases = [("N", "H", 300, 260, 200, 11), ("T", "N", 130, 70, 45, 12),
+             # one tile of C, long k: K shares whose partial products sit in
+             # the scratch after the split operands
+             ("N", "N", 64, 64, 8192, 13)]
     for opA, opB, m, n, k, seed in cases:
         alpha, beta = qsynth.unit_quaternion(seed), qsynth.unit_quaternion(seed + 1)
         A, B, C = make_case(opA, opB, m, n, k, layout, seed, dtype=np.float32)
@@ -49,7 +52,7 @@ def test_noalloc_matches_workspace_entry_point_twice(layout):
 
 def test_noalloc_rejects_problems_beyond_the_scratch():
     L = _abi.lib()
-    n = 745  # smallest square size whose split operands exceed the scratch
+    n = 1181  # smallest square size whose split operands exceed the scratch
     assert L.qgemm_workspace_bytes(0, 0, n, n, n, 0, 1) > _abi.NOALLOC_SCRATCH_BYTES
     X = torch.zeros((n, n, 4), dtype=torch.float32, device="cuda")
     before = X.clone()
