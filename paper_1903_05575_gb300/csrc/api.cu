@@ -379,7 +379,7 @@ int qgemm_debug_arm_fault(int path, int stage, uint64_t limit_ns) {
 }
 
 int qgemm_probe_peak(int which, double seconds, double *tflops, void *stream) {
-  if (which < 0 || which > 14) return -1;
+  if (which < 0 || which > 22) return -1;
   if (!(seconds > 0.0) || seconds > 60.0) return -2;
   if (tflops == nullptr) return -3;
   int rc = device_ready();

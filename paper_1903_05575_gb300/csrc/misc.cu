@@ -96,7 +96,7 @@ int misc_take_device_error() {
 }
 
 int probe_peak(int which, double seconds, double *tflops, cudaStream_t stream) {
-  if ((which >= 3 && which <= 6) || (which >= 8 && which <= 14))
+  if ((which >= 3 && which <= 6) || (which >= 8 && which <= 22))
     return probe_tcgen05_bf16(which, seconds, tflops, stream);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);

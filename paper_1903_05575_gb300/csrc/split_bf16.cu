@@ -9,6 +9,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <set>
+#include <utility>
 
 #include "split_core.cuh"
 
@@ -186,6 +188,216 @@ __global__ void __launch_bounds__(128, 1) tc_plane_probe_kernel(int iters, uint6
   }
 }
 
+// Alternative MMA orders of one stage for the stage probe (4 x 4 planes):
+// 1 the natural order (A term outer: hh hm hl, mh mm, lh) in (term, plane,
+// sign) collector groups; 2 the GEMM's order without the collector; 3 the
+// GEMM's passes with planes j outer and B terms inner in each group; 4 only
+// the hh products, six times (the plane pattern within the stage layout).
+template <int ORDER>
+__device__ __forceinline__ void issue_stage_alt(uint32_t d0, uint64_t adesc, uint64_t bdesc,
+                                                uint32_t idesc_n) {
+  constexpr int kPassTa[6] = {0, 1, 2, 0, 0, 0};
+  constexpr int kPassTb0[6] = {0, 0, 0, 0, 0, 0};
+  constexpr int kPassTb1[6] = {2, 1, 0, 0, 0, 0};
+  constexpr int kGemmTa[4] = {2, 1, 0, 0};
+  constexpr int kGemmTb0[4] = {0, 0, 1, 0};
+  constexpr int kGemmTb1[4] = {0, 1, 2, 0};
+  constexpr int npass = ORDER == 1 ? 3 : (ORDER == 4 ? 6 : 4);
+#pragma unroll
+  for (int pass = 0; pass < npass; ++pass) {
+    const int ta = ORDER == 1 ? kPassTa[pass] : (ORDER == 4 ? 0 : kGemmTa[pass]);
+    const int tb0 = ORDER == 1 ? kPassTb0[pass] : (ORDER == 4 ? 0 : kGemmTb0[pass]);
+    const int tb1 = ORDER == 1 ? kPassTb1[pass] : (ORDER == 4 ? 0 : kGemmTb1[pass]);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const uint64_t ad = adesc + (((ta * 4 + p) * kAPlaneBytes) >> 4);
+#pragma unroll
+      for (int sg = 0; sg < 2; ++sg) {
+        const uint32_t grp = sign_group(p, sg);
+        if (grp == 0) continue;
+        const int jf = low_bit(grp), jl = high_bit(grp);
+        const uint32_t id = idesc_n | (sg ? kNegB : 0u);
+#pragma unroll
+        for (int o = 0; o < 3 * 4; ++o) {
+          const int tb = ORDER == 3 ? tb0 + o % 3 : tb0 + o / 4;
+          const int j = ORDER == 3 ? o / 3 : o % 4;
+          if (tb > tb1 || j > 3 || !((grp >> j) & 1u)) continue;
+          const uint64_t bd = bdesc + (((tb * 4 + j) * kBPlaneBytes) >> 4);
+          const uint32_t d = d0 + (p ^ j) * BNQ;
+          const bool first = ORDER == 3 ? (j == jf && tb == tb0) : (tb == tb0 && j == jf);
+          const bool last = ORDER == 3 ? (j == jl && tb == tb1) : (tb == tb1 && j == jl);
+          if (ORDER == 2 || (first && last))
+            umma_bf16(d, ad, bd, id, 1u);
+          else if (first)
+            umma_bf16_fill(d, ad, bd, id, 1u);
+          else if (last)
+            umma_bf16_lastuse(d, ad, bd, id, 1u);
+          else
+            umma_bf16_use(d, ad, bd, id, 1u);
+        }
+      }
+    }
+  }
+}
+
+// Stage probe: the GEMM's own MMA stream (issue_stage<4, 4>: 96 MMAs per
+// 16-kappa stage) over three stage slots of the ring and the two TMEM
+// accumulator sets, one commit per stage; with THROTTLE the issuer also waits
+// for the commit two stages back before reusing an accumulator set, as the
+// GEMM waits for the drain.  No TMA, no drain: the ceiling of the MMA issue.
+template <bool THROTTLE, int ORDER>
+__global__ void __launch_bounds__(128, 1) tc_stage_probe_kernel(int iters, uint64_t limit_ns) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uint32_t raw_addr = smem_u32(smem_raw);
+  unsigned char *buf = smem_raw + ((1024 - (raw_addr & 1023)) & 1023);
+  __shared__ uint64_t bar[2], done;
+  __shared__ uint32_t tbase;
+  const int warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < static_cast<int>(STAGES * kStageBytes / 4); i += blockDim.x) {
+    const uint32_t h0 = (2u * i + 1u) * 2654435761u, h1 = (2u * i + 2u) * 2654435761u;
+    const float f0 = static_cast<float>(static_cast<int>((h0 >> 16) % 255u) - 127);
+    const float f1 = static_cast<float>(static_cast<int>((h1 >> 16) % 255u) - 127);
+    reinterpret_cast<uint32_t *>(buf)[i] = (__float_as_uint(f0) >> 16) | (__float_as_uint(f1) & 0xffff0000u);
+  }
+  fence_proxy_async_smem();
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init(&done, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) tmem_alloc(&tbase, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0 && elect_one()) {
+    const uint32_t idesc = idesc_bf16(BM, BNQ);
+    const uint32_t ring = smem_u32(buf);
+    bool ok = true;
+    for (int it = 0; it < iters && ok; ++it) {
+      const int b = it & 1;
+      if (THROTTLE && it >= 2) {
+        ok = mbar_wait_bounded(&bar[b], ((it - 2) >> 1) & 1, limit_ns);
+        tc_fence_after();
+      }
+      const uint32_t sa = ring + (it % STAGES) * kStageBytes;
+      if (ORDER == 0)
+        issue_stage<4, 4>(tbase + b * kBufCols, smem_desc_sw32(sa), smem_desc_sw32(sa + kStageA),
+                          idesc, it >= 2);
+      else
+        issue_stage_alt<ORDER>(tbase + b * kBufCols, smem_desc_sw32(sa),
+                               smem_desc_sw32(sa + kStageA), idesc);
+      umma_commit(&bar[b]);
+    }
+    // every MMA issued by this thread completes before TMEM is released
+    umma_commit(&done);
+    if (!mbar_wait_bounded(&done, 0, limit_ns) || !ok) atomicCAS(&g_split_error, 0, QGEMM_ERR_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tbase, kTmemCols);
+  }
+}
+
+// Pipeline probe: the GEMM's MMA stream inside the GEMM's warp roles, without
+// data movement or drain work.  MODE 1: a producer warp and the MMA warp pass
+// the three ring stages through full / empty barriers (the producer arrives
+// instead of copying); MODE 2: also eight drain warps that take each chunk's
+// accumulator set (accfull) and hand it back (accempty) without reading it.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) tc_pipe_probe_kernel(int iters, uint64_t limit_ns) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uint32_t raw_addr = smem_u32(smem_raw);
+  unsigned char *ring = smem_raw + ((1024 - (raw_addr & 1023)) & 1023);
+  SmemCtl *ctl = reinterpret_cast<SmemCtl *>(ring + STAGES * kStageBytes);
+  const int warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < static_cast<int>(STAGES * kStageBytes / 4); i += blockDim.x) {
+    const uint32_t h0 = (2u * i + 1u) * 2654435761u, h1 = (2u * i + 2u) * 2654435761u;
+    const float f0 = static_cast<float>(static_cast<int>((h0 >> 16) % 255u) - 127);
+    const float f1 = static_cast<float>(static_cast<int>((h1 >> 16) % 255u) - 127);
+    reinterpret_cast<uint32_t *>(ring)[i] = (__float_as_uint(f0) >> 16) | (__float_as_uint(f1) & 0xffff0000u);
+  }
+  fence_proxy_async_smem();
+  if (threadIdx.x == 0) {
+    for (int s2 = 0; s2 < STAGES; ++s2) {
+      mbar_init(&ctl->full[s2], 1);
+      mbar_init(&ctl->empty[s2], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&ctl->accfull[b], 1);
+      mbar_init(&ctl->accempty[b], kEpiWarps);
+    }
+    mbar_init(&ctl->done, 1);
+    ctl->abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(&ctl->tmem_base, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ctl->tmem_base;
+  if (warp == 0) {
+    if (elect_one()) {
+      for (int s_run = 0; s_run < iters; ++s_run) {
+        const int st = s_run % STAGES;
+        if (!wait_phase(&ctl->empty[st], ((s_run / STAGES) & 1) ^ 1, limit_ns, ctl)) {
+          set_abort<SplitErr>(ctl);
+          break;
+        }
+        mbar_arrive(&ctl->full[st]);
+      }
+    }
+  } else if (warp == 1) {
+    if (elect_one()) {
+      const uint32_t idesc = idesc_bf16(BM, BNQ);
+      const uint32_t ring_addr = smem_u32(ring);
+      for (int s_run = 0; s_run < iters; ++s_run) {
+        const int st = s_run % STAGES, b = s_run & 1;
+        if (MODE == 2) {
+          if (!wait_phase(&ctl->accempty[b], ((s_run >> 1) & 1) ^ 1, limit_ns, ctl)) {
+            set_abort<SplitErr>(ctl);
+            break;
+          }
+          tc_fence_after();
+        }
+        if (!wait_phase(&ctl->full[st], (s_run / STAGES) & 1, limit_ns, ctl)) {
+          set_abort<SplitErr>(ctl);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = ring_addr + st * kStageBytes;
+        issue_stage<4, 4>(tmem + b * kBufCols, smem_desc_sw32(sa), smem_desc_sw32(sa + kStageA),
+                          idesc, s_run >= 2);
+        umma_commit(&ctl->empty[st]);
+        if (MODE == 2) umma_commit(&ctl->accfull[b]);
+      }
+      umma_commit(&ctl->done);
+      mbar_wait_bounded(&ctl->done, 0, limit_ns);
+    }
+  } else if (warp >= 4 && MODE == 2) {
+    const int lane = threadIdx.x & 31;
+    for (int c_run = 0; c_run < iters; ++c_run) {
+      const int b = c_run & 1;
+      if (!wait_phase(&ctl->accfull[b], (c_run >> 1) & 1, limit_ns, ctl)) {
+        set_abort<SplitErr>(ctl);
+        break;
+      }
+      tc_fence_after();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ctl->accempty[b]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
 // ----------------------------------------------------------- host side ---
 struct SplitPlan {
   int64_t kp;           // kappa pitch of the split operands (multiple of 8)
@@ -276,20 +488,24 @@ bool encode_split_planes(CUtensorMap *map, const void *base, int64_t kq, int64_t
 
 namespace {
 
+// Raises the dynamic shared-memory limit of one kernel, once per (kernel,
+// device).  Keyed by the kernel's address: kernels of one signature share a
+// type, so a per-type flag would skip all but the first of them.
 template <typename K>
 int set_smem(K kern, size_t bytes) {
-  static bool done[64];
+  static std::mutex mu;
+  static std::set<std::pair<const void *, int>> done;
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) return QGEMM_ERR_UNSUPPORTED;
-  if (!done[dev]) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(bytes)) != cudaSuccess) {
-      cudaGetLastError();
-      return QGEMM_ERR_CUDA;
-    }
-    done[dev] = true;
+  const std::pair<const void *, int> key(reinterpret_cast<const void *>(kern), dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count(key)) return QGEMM_SUCCESS;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(bytes)) != cudaSuccess) {
+    cudaGetLastError();
+    return QGEMM_ERR_CUDA;
   }
+  done.insert(key);
   return QGEMM_SUCCESS;
 }
 
@@ -564,8 +780,85 @@ int probe_plane_pattern(double seconds, double *tflops, cudaStream_t stream) {
   return rc;
 }
 
+template <bool THROTTLE, int ORDER>
+int probe_stage_pattern(double seconds, double *tflops, cudaStream_t stream) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = 1024 + STAGES * kStageBytes;
+  int rc = set_smem(tc_stage_probe_kernel<THROTTLE, ORDER>, smem);
+  if (rc) return rc;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int iters = 64;
+  float ms = 0.f;
+  for (int round = 0; round < 8; ++round) {
+    cudaEventRecord(e0, stream);
+    tc_stage_probe_kernel<THROTTLE, ORDER><<<sms, 128, smem, stream>>>(iters, wait_limit_ns());
+    cudaEventRecord(e1, stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = QGEMM_ERR_CUDA;
+      break;
+    }
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms >= 0.5 * seconds * 1e3) break;
+    double scale = (seconds * 1e3) / (ms > 0.01 ? ms : 0.01);
+    if (scale > 64) scale = 64;
+    iters = static_cast<int>(iters * scale);
+    if (iters > (1 << 22)) iters = 1 << 22;
+  }
+  if (rc == QGEMM_SUCCESS && cudaGetLastError() != cudaSuccess) rc = QGEMM_ERR_CUDA;
+  if (rc == QGEMM_SUCCESS) *tflops = 2.0 * BM * BNQ * KQ * 96.0 * iters * sms / (ms * 1e-3) / 1e12;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+template <int MODE>
+int probe_pipe_pattern(double seconds, double *tflops, cudaStream_t stream) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int rc = set_smem(tc_pipe_probe_kernel<MODE>, kSmemBytes);
+  if (rc) return rc;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int iters = 64;
+  float ms = 0.f;
+  for (int round = 0; round < 8; ++round) {
+    cudaEventRecord(e0, stream);
+    tc_pipe_probe_kernel<MODE><<<sms, kThreads, kSmemBytes, stream>>>(iters, wait_limit_ns());
+    cudaEventRecord(e1, stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = QGEMM_ERR_CUDA;
+      break;
+    }
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms >= 0.5 * seconds * 1e3) break;
+    double scale = (seconds * 1e3) / (ms > 0.01 ? ms : 0.01);
+    if (scale > 64) scale = 64;
+    iters = static_cast<int>(iters * scale);
+    if (iters > (1 << 22)) iters = 1 << 22;
+  }
+  if (rc == QGEMM_SUCCESS && cudaGetLastError() != cudaSuccess) rc = QGEMM_ERR_CUDA;
+  if (rc == QGEMM_SUCCESS) *tflops = 2.0 * BM * BNQ * KQ * 96.0 * iters * sms / (ms * 1e-3) / 1e12;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
 int probe_tcgen05_bf16(int which, double seconds, double *tflops, cudaStream_t stream) {
   switch (which) {
+    case 21: return probe_pipe_pattern<1>(seconds, tflops, stream);
+    case 22: return probe_pipe_pattern<2>(seconds, tflops, stream);
+    case 15: return probe_stage_pattern<false, 0>(seconds, tflops, stream);
+    case 16: return probe_stage_pattern<true, 0>(seconds, tflops, stream);
+    case 17: return probe_stage_pattern<false, 1>(seconds, tflops, stream);
+    case 18: return probe_stage_pattern<false, 2>(seconds, tflops, stream);
+    case 19: return probe_stage_pattern<false, 3>(seconds, tflops, stream);
+    case 20: return probe_stage_pattern<false, 4>(seconds, tflops, stream);
     case 13: return probe_plane_pattern<32>(seconds, tflops, stream);
     case 14: return probe_plane_pattern<128>(seconds, tflops, stream);
     case 3: return probe_tcgen05_shape<256, false, 1, false>(seconds, tflops, stream);
