@@ -424,9 +424,13 @@ int prepare_split(const std::vector<GemmDesc> &ds_in, int layout, unsigned char 
       for (int r = 0; r < (d.n + 31) / 32; ++r)
         for (int c = 0; c < kt; ++c) ptiles.push_back(make_int4(static_cast<int>(p), 1, r, c));
     }
+    if (q.g.num_kb >= (1 << 24)) return QGEMM_ERR_UNSUPPORTED;
     for (int a = 0; a < q.g.num_mt; ++a)
       for (int b = 0; b < q.g.num_nt; ++b) {
-        tiles.push_back(make_int4(static_cast<int>(p), a, b, 0));
+        // w: the tile's stages and MMA width, so the kernel needs no parameter
+        // load to start it
+        const int w = q.g.num_kb | (split::tile_ncols(q.g, b) << 24);
+        tiles.push_back(make_int4(static_cast<int>(p), a, b, w));
         tile_kb.push_back(q.g.num_kb);
       }
   }

@@ -652,6 +652,49 @@ __device__ __forceinline__ void tile_of(int t, const GemmParams &single, const C
   }
 }
 
+// Everything a role needs to know about tile t.  Grouped tiles carry their
+// stage count and MMA width in the tile entry (w = stages | width << 24) and
+// are plain quaternion products, so no role waits on the problem's
+// parameters in global memory before it can start the tile.
+struct TileInfo {
+  const GemmParams *g;
+  const CUtensorMap *mA, *mB;
+  int mt, nt, z;
+  int kb_lo, kb_hi;  // stages of the tile (its share when K is split)
+  int ncols;         // MMA width: valid quaternion columns rounded up to 16
+  int pa, pb;        // planes of the A and B operands
+  bool skip;         // no element of the tile in the stored triangle of C
+};
+
+template <bool GROUPED>
+__device__ __forceinline__ TileInfo tile_info(int t, int4 e, const GemmParams &single,
+                                              const CUtensorMap *smA, const CUtensorMap *smB,
+                                              const SplitProb *probs) {
+  TileInfo ti;
+  if (GROUPED) {
+    const SplitProb *pr = probs + e.x;
+    ti.g = &pr->g;
+    ti.mA = &pr->tmA;
+    ti.mB = &pr->tmB;
+    ti.mt = e.y;
+    ti.nt = e.z;
+    ti.z = 0;
+    ti.kb_lo = 0;
+    ti.kb_hi = e.w & 0xFFFFFF;
+    ti.ncols = (e.w >> 24) & 0xFF;
+    ti.pa = ti.pb = PLANES;
+    ti.skip = false;
+  } else {
+    tile_of<false>(t, single, smA, smB, probs, nullptr, ti.g, ti.mA, ti.mB, ti.mt, ti.nt, ti.z);
+    ti.skip = tile_skip(single, ti.mt, ti.nt);
+    kb_range(single, ti.mt, ti.nt, ti.z, ti.kb_lo, ti.kb_hi);
+    ti.ncols = tile_ncols(single, ti.nt);
+    ti.pa = single.pa;
+    ti.pb = single.pb;
+  }
+  return ti;
+}
+
 // Address of element (ci, cj) of C: the first component (interleaved) or the
 // component-0 plane entry (planes).
 __device__ __forceinline__ float *c_elem(const GemmParams &g, int64_t ci, int64_t cj) {
@@ -678,86 +721,103 @@ __device__ __forceinline__ void prefetch_c(const GemmParams &g, int64_t i, int64
   }
 }
 
-// Epilogue of one tile for one drain thread: row i, 32 quaternion columns
-// starting at nbase, accumulated P in packed pairs: component c of column q
-// is word q % 2 of acc[16 c + q / 2].
-// out = P + beta C (beta on the left), in double-float with one rounding.  C
-// is read in batches of kCBatch elements, all loads of a batch before its
-// stores.
 constexpr int kCBatch = 4;
 __device__ __forceinline__ float acc_at(const uint64_t (&acc)[64], int c, int q) {
   return (q & 1) ? hi_of(acc[16 * c + (q >> 1)]) : lo_of(acc[16 * c + (q >> 1)]);
 }
+struct PBatch {
+  float p[kCBatch][4];  // P of kCBatch consecutive columns, components 0..3
+};
+
+// out = P + beta C for kCBatch columns from n0 of row i.  Not inlined: one
+// copy of this code serves the tile's eight batches, which keeps the
+// kernel's instruction working set small (small grouped tiles run the
+// epilogue often, and an unrolled copy evicted the hot loops from the
+// instruction cache).
+static __device__ __noinline__ void epilogue_batch(const GemmParams &g, int64_t i, int64_t n0,
+                                            PBatch pb) {
+  float cin[kCBatch][4];
+#pragma unroll
+  for (int u = 0; u < kCBatch; ++u) {
+    const int64_t nn = n0 + u;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) cin[u][s] = 0.f;
+    if (g.beta_zero || nn >= g.n) continue;
+    // element (ci, cj) of C; a transposed problem holds (AB)^H: take conj(D)^T
+    const int64_t ci = g.swap ? nn : i, cj = g.swap ? i : nn;
+    const float *src = c_elem(g, ci, cj);
+    if (g.layout == QGEMM_INTERLEAVED && g.c_vec4) {
+      const float4 c4 = *reinterpret_cast<const float4 *>(src);
+      cin[u][0] = c4.x; cin[u][1] = c4.y; cin[u][2] = c4.z; cin[u][3] = c4.w;
+    } else {
+      const int64_t step = g.layout == QGEMM_INTERLEAVED ? 1 : g.psC;
+#pragma unroll
+      for (int s = 0; s < 4; ++s) cin[u][s] = src[s * step];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kCBatch; ++u) {
+    const int64_t nn = n0 + u;
+    if (nn >= g.n) continue;
+    if ((g.tri == 1 && i < nn) || (g.tri == 2 && i > nn)) continue;
+    float P[4] = {pb.p[u][0], pb.p[u][1], pb.p[u][2], pb.p[u][3]};
+    const int64_t ci = g.swap ? nn : i, cj = g.swap ? i : nn;
+    if (g.swap) {
+      P[1] = -P[1];
+      P[2] = -P[2];
+      P[3] = -P[3];
+    }
+    float out[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float hi = P[c], lo = 0.f;
+      if (!g.beta_zero) {
+        if (g.beta_real) {
+          df_fma(hi, lo, g.beta_hi[0], g.beta_lo[0], cin[u][c]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int s = c ^ j;  // the sign is a compile-time constant here
+            const bool neg = basis_sign(s, j) < 0;
+            df_fma(hi, lo, neg ? -g.beta_hi[s] : g.beta_hi[s], neg ? -g.beta_lo[s] : g.beta_lo[s],
+                   cin[u][j]);
+          }
+        }
+      }
+      out[c] = __fadd_rn(hi, lo);
+    }
+    if (g.tri && i == nn) out[1] = out[2] = out[3] = 0.f;  // Hermitian diagonal is real
+    float *dst0 = c_elem(g, ci, cj);
+    if (g.layout == QGEMM_INTERLEAVED) {
+      if (g.c_vec4)
+        *reinterpret_cast<float4 *>(dst0) = make_float4(out[0], out[1], out[2], out[3]);
+      else
+#pragma unroll
+        for (int s = 0; s < 4; ++s) dst0[s] = out[s];
+    } else {
+#pragma unroll
+      for (int s = 0; s < 4; ++s) dst0[s * g.psC] = out[s];
+    }
+  }
+}
+
+// Epilogue of one tile for one drain thread: row i, 32 quaternion columns
+// starting at nbase, accumulated P in packed pairs (component c of column q
+// is word q % 2 of acc[16 c + q / 2]); out = P + beta C (beta on the left)
+// in double-float with one rounding, kCBatch columns per call.
 __device__ __forceinline__ void epilogue(const GemmParams &g, int64_t i, int64_t nbase,
                                          const uint64_t (&acc)[64]) {
   if (i >= g.m) return;
   if (g.tri == 2 && nbase + 31 < i) return;
 #pragma unroll
   for (int qb = 0; qb < 32; qb += kCBatch) {
-    float cin[kCBatch][4];
+    if (nbase + qb >= g.n) break;
+    PBatch pb;
 #pragma unroll
-    for (int u = 0; u < kCBatch; ++u) {
-      const int64_t nn = nbase + qb + u;
+    for (int u = 0; u < kCBatch; ++u)
 #pragma unroll
-      for (int s = 0; s < 4; ++s) cin[u][s] = 0.f;
-      if (g.beta_zero || nn >= g.n) continue;
-      // element (ci, cj) of C; a transposed problem holds (AB)^H: take conj(D)^T
-      const int64_t ci = g.swap ? nn : i, cj = g.swap ? i : nn;
-      const float *src = c_elem(g, ci, cj);
-      if (g.layout == QGEMM_INTERLEAVED && g.c_vec4) {
-        const float4 c4 = *reinterpret_cast<const float4 *>(src);
-        cin[u][0] = c4.x; cin[u][1] = c4.y; cin[u][2] = c4.z; cin[u][3] = c4.w;
-      } else {
-        const int64_t step = g.layout == QGEMM_INTERLEAVED ? 1 : g.psC;
-#pragma unroll
-        for (int s = 0; s < 4; ++s) cin[u][s] = src[s * step];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kCBatch; ++u) {
-      const int q = qb + u;
-      const int64_t nn = nbase + q;
-      if (nn >= g.n) continue;
-      if ((g.tri == 1 && i < nn) || (g.tri == 2 && i > nn)) continue;
-      float P[4] = {acc_at(acc, 0, q), acc_at(acc, 1, q), acc_at(acc, 2, q), acc_at(acc, 3, q)};
-      const int64_t ci = g.swap ? nn : i, cj = g.swap ? i : nn;
-      if (g.swap) {
-        P[1] = -P[1];
-        P[2] = -P[2];
-        P[3] = -P[3];
-      }
-      float out[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        float hi = P[c], lo = 0.f;
-        if (!g.beta_zero) {
-          if (g.beta_real) {
-            df_fma(hi, lo, g.beta_hi[0], g.beta_lo[0], cin[u][c]);
-          } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const int s = c ^ j;  // the sign is a compile-time constant here
-              const bool neg = basis_sign(s, j) < 0;
-              df_fma(hi, lo, neg ? -g.beta_hi[s] : g.beta_hi[s],
-                     neg ? -g.beta_lo[s] : g.beta_lo[s], cin[u][j]);
-            }
-          }
-        }
-        out[c] = __fadd_rn(hi, lo);
-      }
-      if (g.tri && i == nn) out[1] = out[2] = out[3] = 0.f;  // Hermitian diagonal is real
-      float *dst0 = c_elem(g, ci, cj);
-      if (g.layout == QGEMM_INTERLEAVED) {
-        if (g.c_vec4)
-          *reinterpret_cast<float4 *>(dst0) = make_float4(out[0], out[1], out[2], out[3]);
-        else
-#pragma unroll
-          for (int s = 0; s < 4; ++s) dst0[s] = out[s];
-      } else {
-#pragma unroll
-        for (int s = 0; s < 4; ++s) dst0[s * g.psC] = out[s];
-      }
-    }
+      for (int c = 0; c < 4; ++c) pb.p[u][c] = acc_at(acc, c, qb + u);
+    epilogue_batch(g, i, nbase + qb, pb);
   }
 }
 
@@ -929,17 +989,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       uint32_t s_run = 0;
       bool ok = true;
+      int4 e_next = make_int4(0, 0, 0, 0);
+      if (GROUPED && static_cast<int>(blockIdx.x) < ntiles) e_next = tiles[blockIdx.x];
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const GemmParams *g;
-        const CUtensorMap *mA, *mB;
-        int mt, nt, z;
-        tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt, z);
-        if (tile_skip(*g, mt, nt)) continue;
-        int kb_lo, kb_hi;
-        kb_range(*g, mt, nt, z, kb_lo, kb_hi);
-        const uint32_t bytes = static_cast<uint32_t>(g->pa) * TERMS * kAPlaneBytes +
-                               static_cast<uint32_t>(g->pb) * TERMS * kBPlaneBytes;
-        for (int kb = kb_lo; kb < kb_hi; ++kb, ++s_run) {
+        const int4 e = e_next;  // the next entry loads while this tile runs
+        if (GROUPED && t + static_cast<int>(gridDim.x) < ntiles) e_next = tiles[t + gridDim.x];
+        const TileInfo ti = tile_info<GROUPED>(t, e, single, &tmA, &tmB, probs);
+        if (ti.skip) continue;
+        const CUtensorMap *mA = ti.mA, *mB = ti.mB;
+        const int mt = ti.mt, nt = ti.nt;
+        const uint32_t bytes = static_cast<uint32_t>(ti.pa) * TERMS * kAPlaneBytes +
+                               static_cast<uint32_t>(ti.pb) * TERMS * kBPlaneBytes;
+        for (int kb = ti.kb_lo; kb < ti.kb_hi; ++kb, ++s_run) {
           const int st = s_run % STAGES;
           if (!wait_phase(&ctl->empty[st], ((s_run / STAGES) & 1) ^ 1, limit_ns, ctl)) {
             set_abort<Err>(ctl);
@@ -962,18 +1023,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t ring_addr = smem_u32(ring);
       uint32_t s_run = 0, c_run = 0;
       bool ok = true;
+      int4 e_next = make_int4(0, 0, 0, 0);
+      if (GROUPED && static_cast<int>(blockIdx.x) < ntiles) e_next = tiles[blockIdx.x];
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const GemmParams *g;
-        const CUtensorMap *mA, *mB;
-        int mt, nt, z;
-        tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt, z);
-        if (tile_skip(*g, mt, nt)) continue;
-        int kb_lo, nkb;
-        kb_range(*g, mt, nt, z, kb_lo, nkb);
-        const uint32_t idesc = idesc_bf16(BM, tile_ncols(*g, nt));
-        const int pa = g->pa, pb = g->pb;
+        const int4 e = e_next;  // the next entry loads while this tile runs
+        if (GROUPED && t + static_cast<int>(gridDim.x) < ntiles) e_next = tiles[t + gridDim.x];
+        const TileInfo ti = tile_info<GROUPED>(t, e, single, &tmA, &tmB, probs);
+        if (ti.skip) continue;
+        const int nkb = ti.kb_hi;
+        const uint32_t idesc = idesc_bf16(BM, ti.ncols);
+        const int pa = ti.pa, pb = ti.pb;
         int ch = 0;
-        for (int kb = kb_lo; kb < nkb && ok; ++c_run, ++ch) {
+        for (int kb = ti.kb_lo; kb < nkb && ok; ++c_run, ++ch) {
           const int b = c_run & 1;
           if (!wait_phase(&ctl->accempty[b], ((c_run >> 1) & 1) ^ 1, limit_ns, ctl)) {
             set_abort<Err>(ctl);
@@ -1016,18 +1077,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t lane_base = static_cast<uint32_t>(32 * quad) << 16;
     uint32_t c_run = 0;
     bool ok = true;
+    int4 e_next = make_int4(0, 0, 0, 0);
+    if (GROUPED && static_cast<int>(blockIdx.x) < ntiles) e_next = tiles[blockIdx.x];
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const GemmParams *g;
-      const CUtensorMap *mA, *mB;
-      int mt, nt, z;
-      tile_of<GROUPED>(t, single, &tmA, &tmB, probs, tiles, g, mA, mB, mt, nt, z);
-      if (tile_skip(*g, mt, nt)) continue;
-      int kb_lo, kb_hi;
-      kb_range(*g, mt, nt, z, kb_lo, kb_hi);
-      const int nch = (kb_hi - kb_lo + kChunk - 1) / kChunk;
-      const bool mine = 32 * half < tile_ncols(*g, nt);  // this warp's columns hold data
-      const int nacc = g->pa > g->pb ? g->pa : g->pb;    // components the MMAs write
-      if (g->ksplit <= 1 && mine)
+      const int4 e = e_next;  // the next entry loads while this tile runs
+      if (GROUPED && t + static_cast<int>(gridDim.x) < ntiles) e_next = tiles[t + gridDim.x];
+      const TileInfo ti = tile_info<GROUPED>(t, e, single, &tmA, &tmB, probs);
+      if (ti.skip) continue;
+      const GemmParams *g = ti.g;
+      const int mt = ti.mt, nt = ti.nt, z = ti.z;
+      const int nch = (ti.kb_hi - ti.kb_lo + kChunk - 1) / kChunk;
+      const bool mine = 32 * half < ti.ncols;          // this warp's columns hold data
+      const int nacc = ti.pa > ti.pb ? ti.pa : ti.pb;  // components the MMAs write
+      const bool split_k = !GROUPED && single.ksplit > 1;  // grouped problems never split K
+      if (!split_k && mine)
         prefetch_c(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane,
                    static_cast<int64_t>(nt) * BNQ + 32 * half);
       uint64_t acc[64];  // packed pairs: component c, columns 2i, 2i + 1 in acc[16 c + i]
@@ -1079,7 +1142,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!ok) break;
       if (!mine) continue;
-      if (g->ksplit > 1)
+      if (split_k)
         store_partial(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane,
                       static_cast<int64_t>(nt) * BNQ + 32 * half, z, acc);
       else
