@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--no-grouped", action="store_true")
     p.add_argument("--grouped-count", type=int, default=4096)
     p.add_argument("--no-linear", action="store_true")
+    p.add_argument("--no-complex", action="store_true")
+    p.add_argument("--complex-size", type=int, default=4096)
     return p.parse_args()
 
 
@@ -333,16 +335,39 @@ def split_section(n, fp64_tflops, steps=5):
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     eff = 32.0 * n ** 3 / (ms * 1e-3) / 1e12
-    # error of one result on sampled entries (sampled_reference, FP64)
-    C.copy_(C0)
-    step(C)
-    torch.cuda.synchronize()
-    g = np.random.default_rng(9)
-    rows, cols = g.integers(0, n, 512), g.integers(0, n, 512)
-    Ah, Bh, Ch = (X.double().cpu().numpy() for X in (A, B, C0))
-    ref = sampled_reference("N", "N", n, n, n, alpha, Ah, Bh, beta, Ch, rows, cols)
-    got = qsynth.components(C.double().cpu().numpy(), n, "interleaved")[rows, cols]
-    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+    def sampled_err(Ad, Bd, Cd0, m_, n_, k_, count=512, seed=9):
+        """Error of one result on sampled entries (sampled_reference, FP64)."""
+        need_ = L.qgemm_workspace_bytes(0, 0, m_, n_, k_, 0, 1)
+        ws_ = torch.empty(need_, dtype=torch.uint8, device=dev)
+        Cd = Cd0.clone()
+        rc = L.qgemm(0, 0, m_, n_, k_, al, Ad.data_ptr(), m_, 0, Bd.data_ptr(), k_, 0, be,
+                     Cd.data_ptr(), m_, 0, 0, 1, ws_.data_ptr(), need_, stream.cuda_stream)
+        if rc != 0:
+            raise _abi.QgemmError(rc)
+        torch.cuda.synchronize()
+        g = np.random.default_rng(seed)
+        rows, cols = g.integers(0, m_, count), g.integers(0, n_, count)
+        Ah, Bh, Ch = (X.double().cpu().numpy() for X in (Ad, Bd, Cd0))
+        ref = sampled_reference("N", "N", m_, n_, k_, alpha, Ah, Bh, beta, Ch, rows, cols)
+        got = qsynth.components(Cd.double().cpu().numpy(), m_, "interleaved")[rows, cols]
+        return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+    err = sampled_err(A, B, C0, n, n, n)
+    # wide-range inputs: components N(0,1) 2^(u_r + v_c), u, v integers in
+    # [-20, 20] per stored row and column
+    def scaled(X):
+        u = torch.randint(-20, 21, (X.shape[1],), device=dev, generator=gen)
+        v = torch.randint(-20, 21, (X.shape[0],), device=dev, generator=gen)
+        return X * torch.exp2((u[None, :] + v[:, None]).float())[:, :, None]
+    err_scaled = sampled_err(scaled(A), scaled(B), C0, n, n, n)
+    del C
+    # a long k on one tile of C (the K shares' path): 64 x 64 x 65536
+    kk = 65536
+    Al = torch.randn((kk, 64, 4), dtype=torch.float32, device=dev, generator=gen)
+    Bl = torch.randn((64, kk, 4), dtype=torch.float32, device=dev, generator=gen)
+    Cl = torch.randn((64, 64, 4), dtype=torch.float32, device=dev, generator=gen)
+    err_long = sampled_err(Al, Bl, Cl, 64, 64, kk, count=256)
     peaks = {}
     try:
         peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -358,9 +383,75 @@ def split_section(n, fp64_tflops, steps=5):
             "bf16_peak": bf16_peak,
             "bf16_peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)"
                                 if "bf16_tflops" in peaks else "fallback 1900",
-            "rel_err_sampled": err, "tolerance": 2e-6,
+            "rel_err_sampled": err, "rel_err_sampled_scaled_inputs": err_scaled,
+            "rel_err_sampled_64x64x65536": err_long, "tolerance": 2e-6,
             "speedup_vs_fp64_path": eff / fp64_tflops,
             "kernels_per_call": 3, "workspace_bytes": need, "clocks": clk.summary()}
+
+
+# --------------------------------------------------- complex section ---
+def complex_section(n, steps=1):
+    """The paper's comparison (Sec. 5, Fig. 4; Tab. hc_mat_flops): the same
+    FP64 product P = A B, m = n = k = n quaternions, through cuBLAS ZGEMM on
+    the 2n x 2n complex representation (Eq. qmat_complex: X_C = [[Z1, Z2],
+    [-conj Z2, conj Z1]] with Z1 = X^0 + i X^1, Z2 = X^2 + i X^3) and DGEMM on
+    the 4n x 4n real representation (blocks of L(x)), against this library's
+    QGEMM (op N,N, alpha = 1, beta = 0).  Reports the times, their ratios and
+    the relative difference of each mapped-back result from the QGEMM one."""
+    import torch
+
+    from paper_1903_05575_gb300 import ops
+    dev = torch.device("cuda", torch.cuda.current_device())
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2501)
+    A = torch.randn((n, n, 4), dtype=torch.float64, device=dev, generator=gen)
+    B = torch.randn((n, n, 4), dtype=torch.float64, device=dev, generator=gen)
+    C = torch.empty_like(A)
+    one, zero = (1.0, 0.0, 0.0, 0.0), (0.0, 0.0, 0.0, 0.0)
+
+    def comp(X, c):  # component c as an n x n row-major matrix (X is column-major)
+        return X[:, :, c].transpose(0, 1)
+
+    def to_complex(X):
+        z1 = torch.complex(comp(X, 0), comp(X, 1))
+        z2 = torch.complex(comp(X, 2), comp(X, 3))
+        return torch.cat([torch.cat([z1, z2], 1), torch.cat([-z2.conj(), z1.conj()], 1)], 0)
+
+    def to_real(X):
+        x = [comp(X, c) for c in range(4)]
+        rows = [[x[0], -x[1], -x[2], -x[3]], [x[1], x[0], -x[3], x[2]],
+                [x[2], x[3], x[0], -x[1]], [x[3], -x[2], x[1], x[0]]]
+        return torch.cat([torch.cat(r, 1) for r in rows], 0)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, out
+
+    q_ms, _ = timed(lambda: ops.qgemm("N", "N", n, n, n, one, A, B, zero, C))
+    P = torch.stack([comp(C, c) for c in range(4)])            # 4 x n x n, row-major
+    Ac, Bc = to_complex(A), to_complex(B)
+    z_ms, Zc = timed(lambda: Ac @ Bc)
+    Pz = torch.stack([Zc[:n, :n].real, Zc[:n, :n].imag, Zc[:n, n:].real, Zc[:n, n:].imag])
+    del Ac, Bc, Zc
+    Ar, Br = to_real(A), to_real(B)
+    d_ms, Rr = timed(lambda: Ar @ Br)
+    Pd = torch.stack([Rr[c * n:(c + 1) * n, :n] for c in range(4)])
+    del Ar, Br, Rr
+    nrm = float(torch.linalg.vector_norm(P))
+    return {"n": n, "qgemm_ms": q_ms, "zgemm_ms": z_ms, "dgemm_ms": d_ms,
+            "zgemm_over_qgemm": z_ms / q_ms, "dgemm_over_qgemm": d_ms / q_ms,
+            "zgemm_rel_diff": float(torch.linalg.vector_norm(Pz - P)) / nrm,
+            "dgemm_rel_diff": float(torch.linalg.vector_norm(Pd - P)) / nrm,
+            "qgemm_tflops": 32.0 * n ** 3 / (q_ms * 1e-3) / 1e12,
+            "note": "ZGEMM 2n x 2n complex (8 n^3 complex multiply-adds), DGEMM 4n x 4n real "
+                    "(64 n^3 multiply-adds), QGEMM 16 n^3 real multiply-adds; cuBLAS via torch"}
 
 
 # ---------------------------------------------------- sliced section ---
@@ -798,6 +889,10 @@ def run_ours(args):
         G = qs.components(got, m, layout)[rows, cols]
         err = float(np.linalg.norm(G - ref) / np.linalg.norm(ref))
 
+    cmplx = None
+    if not args.no_complex and world == 1:
+        cmplx = complex_section(args.complex_size)
+
     grouped = grouped_split = grouped_sliced = None
     if not args.no_grouped:
         grouped = grouped_section(args.grouped_count)
@@ -841,13 +936,46 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": args.steps,
         "cpu_baseline": cpu,
-        "split_bf16": split,
-        "fp64_sliced_bf16": sliced,
-        "grouped_fp64": grouped,
-        "grouped_split_bf16": grouped_split,
-        "grouped_fp64_sliced_bf16": grouped_sliced,
-        "linear_layer_split_bf16": linear,
     }
+    # the sections in full on stderr, their key figures on the JSON line
+    # (short enough that a log tail keeps all of it)
+    sections = {"split_bf16": split, "fp64_sliced_bf16": sliced, "grouped_fp64": grouped,
+                "grouped_split_bf16": grouped_split, "grouped_fp64_sliced_bf16": grouped_sliced,
+                "linear_layer_split_bf16": linear, "vs_complex_and_real_gemm": cmplx}
+    for name, sec in sections.items():
+        if sec is not None:
+            print("section %s: %s" % (name, json.dumps(sec)), file=sys.stderr, flush=True)
+
+    def r4(x):
+        return None if x is None else float("%.4g" % x)
+    if split:
+        line["split_bf16"] = {
+            "n": args.split_size, "tflops": r4(split["value"]), "ms": r4(split["ms_per_call"]),
+            "issued_frac": r4(split["frac_of_bf16_peak_issued"]),
+            "err": r4(split["rel_err_sampled"]),
+            "err_scaled": r4(split["rel_err_sampled_scaled_inputs"]),
+            "err_64x64x65536": r4(split["rel_err_sampled_64x64x65536"]),
+            "speedup_vs_fp64": r4(split["speedup_vs_fp64_path"]),
+            "sm_mhz": split["clocks"].get("sm_mhz"), "reasons": split["clocks"].get("reasons")}
+    if sliced:
+        line["fp64_sliced_bf16"] = {
+            "n": args.sliced_size or n, "tflops": r4(sliced["value"]),
+            "ms": r4(sliced["ms_per_call"]), "issued_frac": r4(sliced["frac_of_bf16_peak_issued"]),
+            "err": r4(sliced["rel_err_sampled"]),
+            "speedup_vs_dmma": r4(sliced["speedup_vs_dmma_path"])}
+    for key, sec in (("grouped_fp64", grouped), ("grouped_split_bf16", grouped_split),
+                     ("grouped_fp64_sliced_bf16", grouped_sliced)):
+        if sec:
+            line[key] = {"problems": args.grouped_count, "tflops": r4(sec["value"]),
+                         "ms": r4(sec["ms_per_launch"]), "gbs": r4(sec["achieved_gbs_algorithmic"]),
+                         "err_worst": r4(sec["rel_err_sampled_worst"])}
+    if linear:
+        line["linear_layer_split_bf16"] = {
+            "tflops": r4(linear["value"]), "ms_step": r4(linear["ms_per_step"]),
+            "err_worst": r4(max(linear["rel_err_sampled"].values()))}
+    if cmplx:
+        line["vs_complex_and_real_gemm"] = {
+            k2: (r4(v) if isinstance(v, float) else v) for k2, v in cmplx.items() if k2 != "note"}
     print(json.dumps(line), flush=True)
 
 

@@ -96,7 +96,16 @@ struct SlicedParams {
   double *part;
 };
 
-// Pre-pass arguments of one operand.
+// Pre-pass arguments of one operand.  The maxima are kept as exponents: the
+// largest e(x) over a row, column or kappa, where e(x) is the exponent with
+// 2^(e - 1) <= |x| < 2^e (integer, from the bits of x); kExpEmpty (the memset
+// byte 0x80) when every element is zero, kExpInf when one is Inf or NaN.
+// Kappa balancing: with per-kappa exponents ka, kb of op(A) and op(B), kappa
+// gets t = floor((ka - kb) / 2), and the products use the exact rescaling
+// (A diag(2^-t)) (diag(2^t) B) = A B, so a row of op(A) and a column of
+// op(B) that span many binades along kappa share their largest scales.
+constexpr int kExpInf = 0x40000000;
+constexpr int kExpEmpty = static_cast<int>(0x80808080u);
 struct MaxArgs {
   const double *X;
   int64_t ld, ps;        // stored leading dimension, plane stride
@@ -104,7 +113,11 @@ struct MaxArgs {
   int layout;
   int by_col;            // 0: maxima per stored row, 1: per stored column
   int width;             // components stored per element (4, 2 or 1)
-  unsigned long long *out;
+  int *out;              // exponent maxima (atomicMax)
+  // balancing: 0 none; -1 this is op(A) (exponents e - t); +1 op(B) (e + t).
+  // The kappa of a stored element is its column when by_col = 0, else its row.
+  int tsign;
+  const int *ka, *kb;    // per-kappa exponents of op(A) and op(B)
 };
 
 struct SliceArgs {
@@ -115,8 +128,10 @@ struct SliceArgs {
   int64_t kp;            // padded real K (multiple of SBK)
   int64_t slice_stride;  // elements between slices in the output
   __nv_bfloat16 *out;
-  const unsigned long long *maxbits;  // per op row
-  int *eout;                          // per op row: the exponent used
+  const int *emax;       // per op row: exponent maxima (balanced when tsign != 0)
+  int *eout;             // per op row: the exponent used
+  int tsign;             // balancing as in MaxArgs (-1 for A, +1 for B, 0 none)
+  const int *ka, *kb;    // per-kappa exponents of op(A) and op(B)
   int layout;
   int row_contig;        // stored row index == op row
   uint32_t negmask;      // bit j: negate component j (conjugation)
@@ -734,36 +749,58 @@ __global__ void __launch_bounds__(kSThreads, 1)
 }
 
 // ------------------------------------------------------------ pre-pass ---
-// Largest |component| of each quaternion row (by_col = 0) or column
-// (by_col = 1) of a stored matrix, as the bits of a non-negative double
-// (ordered like the values; NaN above Inf), max-reduced into out[]: one
-// 32 x 32 tile (rt, ct) of the stored matrix per call, 256 threads.
+// e(x): 2^(e - 1) <= |x| < 2^e for finite nonzero x, from the bits of x
+// (integer operations only); kExpEmpty for zero, kExpInf for Inf or NaN.
+__device__ __forceinline__ int elem_exp(double x) {
+  const unsigned long long b =
+      static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7fffffffffffffffull;
+  if (b >= 0x7ff0000000000000ull) return kExpInf;
+  if (b == 0) return kExpEmpty;
+  const int E = static_cast<int>(b >> 52);
+  if (E > 0) return E - 1022;
+  return (63 - __clzll(static_cast<long long>(b))) - 1073;  // subnormal
+}
+
+// The balancing exponent t of one kappa (0 when a kappa maximum is zero or
+// not finite): op(A)'s kappa column scaled by 2^-t and op(B)'s kappa row by
+// 2^t then have the same largest exponent, up to one.
+__device__ __forceinline__ int kappa_balance(const int *ka, const int *kb, int64_t kappa) {
+  const int x = ka[kappa], y = kb[kappa];
+  if (x <= kExpEmpty / 2 || y <= kExpEmpty / 2 || x >= kExpInf || y >= kExpInf) return 0;
+  return (x - y) >> 1;  // floor
+}
+
+// Largest exponent of the components of each quaternion row (by_col = 0) or
+// column (by_col = 1) of a stored matrix, with the kappa balancing of the
+// element when tsign != 0, max-reduced into out[]: one 32 x 32 tile (rt, ct)
+// of the stored matrix per call, 256 threads.
 __device__ __forceinline__ void max_tile(const MaxArgs &a, int64_t rt, int64_t ct,
-                                         unsigned long long (*red)[32]) {
+                                         int (*red)[32]) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int64_t r = rt * 32 + tx;
   const int64_t c0 = ct * 32;
-  unsigned long long rowm = 0;
+  int rowm = kExpEmpty;
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     const int64_t c = c0 + ty + 8 * s;
-    unsigned long long mx = 0;
+    int mx = kExpEmpty;
     if (r < a.srows && c < a.scols) {
       for (int comp = 0; comp < a.width; ++comp) {
         const double x = a.layout == QGEMM_INTERLEAVED ? a.X[a.width * (r + c * a.ld) + comp]
                                                        : a.X[r + c * a.ld + comp * a.ps];
-        const unsigned long long b =
-            static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7fffffffffffffffull;
-        mx = b > mx ? b : mx;
+        const int e = elem_exp(x);
+        mx = e > mx ? e : mx;
       }
+      if (a.tsign != 0 && mx > kExpEmpty && mx < kExpInf)
+        mx += a.tsign * kappa_balance(a.ka, a.kb, a.by_col ? r : c);
     }
     if (a.by_col) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+        const int y = __shfl_xor_sync(0xffffffffu, mx, o);
         mx = y > mx ? y : mx;
       }
-      if (tx == 0 && c < a.scols && mx != 0) atomicMax(a.out + c, mx);
+      if (tx == 0 && c < a.scols && mx != kExpEmpty) atomicMax(a.out + c, mx);
     } else {
       rowm = mx > rowm ? mx : rowm;
     }
@@ -772,16 +809,16 @@ __device__ __forceinline__ void max_tile(const MaxArgs &a, int64_t rt, int64_t c
     red[ty][tx] = rowm;
     __syncthreads();
     if (ty == 0) {
-      unsigned long long v = red[0][tx];
+      int v = red[0][tx];
 #pragma unroll
       for (int w = 1; w < 8; ++w) v = red[w][tx] > v ? red[w][tx] : v;
-      if (r < a.srows && v != 0) atomicMax(a.out + r, v);
+      if (r < a.srows && v != kExpEmpty) atomicMax(a.out + r, v);
     }
   }
 }
 
 __global__ void __launch_bounds__(256) slice_max_kernel(const MaxArgs a) {
-  __shared__ unsigned long long red[8][32];
+  __shared__ int red[8][32];
   max_tile(a, blockIdx.x, blockIdx.y, red);
 }
 
@@ -789,7 +826,7 @@ __global__ void __launch_bounds__(256) slice_max_kernel(const MaxArgs a) {
 __global__ void __launch_bounds__(256)
     grouped_slice_max_kernel(const SlicedProb *__restrict__ probs,
                              const int4 *__restrict__ mtiles, int n) {
-  __shared__ unsigned long long red[8][32];
+  __shared__ int red[8][32];
   for (int t = blockIdx.x; t < n; t += gridDim.x) {
     const int4 e = mtiles[t];
     const SlicedProb &pr = probs[e.x];
@@ -798,15 +835,13 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Exponent e with max < 2^e (0 for a zero row, kNonFinite for Inf or NaN).
-__device__ __forceinline__ int exponent_of(unsigned long long maxbits) {
-  if (maxbits >= 0x7ff0000000000000ull) return kNonFinite;
-  if (maxbits == 0) return 0;
-  int e = 0;
-  frexp(__longlong_as_double(static_cast<long long>(maxbits)), &e);
-  return e;
+// Exponent e with max < 2^e of a row from its maximum: 0 for a zero row,
+// kNonFinite for a row with Inf or NaN.
+__device__ __forceinline__ int row_exponent(int emax) {
+  if (emax >= kExpInf) return kNonFinite;
+  if (emax <= kExpEmpty / 2) return 0;
+  return emax;
 }
-
 
 // round(a 2^s) to the nearest integer (ties to even) for |a| 2^s <= 2^47,
 // from the bits of a: integer operations only (GB300's FP64 pipe is narrow).
@@ -879,7 +914,7 @@ __device__ __forceinline__ void slice_tile(const SliceArgs &p, int64_t rt, int64
     const int64_t r = r0 + threadIdx.x;
     int e = 0;
     if (r < p.rows) {
-      e = exponent_of(p.maxbits[r]);
+      e = row_exponent(p.emax[r]);
       if (kt == 0) p.eout[r] = e;
     }
     sm.shift[threadIdx.x] = e == kNonFinite ? kNonFinite : 47 - e;
@@ -919,7 +954,9 @@ __device__ __forceinline__ void slice_tile(const SliceArgs &p, int64_t rt, int64
     const int64_t r = r0 + rr, kq = k0 + kk;
     if (r >= p.rows || p.kw * kq >= p.kp) continue;
     const double4 v = tile[kk][rr];
-    const int sft = sm.shift[rr];
+    // kappa balancing: op(A) scaled by 2^-t, op(B) by 2^t (exact)
+    const int tk = (p.tsign != 0 && kq < p.kq) ? p.tsign * kappa_balance(p.ka, p.kb, kq) : 0;
+    const int sft = sm.shift[rr] == kNonFinite ? kNonFinite : sm.shift[rr] + tk;
     const double comp[4] = {v.x, v.y, v.z, v.w};
     long long X[4];
 #pragma unroll
@@ -987,7 +1024,7 @@ __global__ void __launch_bounds__(256, IS_B ? 5 : 6)
 // ----------------------------------------------------------- host side ---
 struct SlicedPlan {
   int64_t kp;
-  size_t a_off, b_off, maxa_off, maxb_off, ea_off, eb_off, total;
+  size_t a_off, b_off, maxa_off, maxb_off, ka_off, kb_off, ea_off, eb_off, total;
 };
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -1000,8 +1037,10 @@ SlicedPlan plan_for(const GemmDesc &d) {
   s.b_off = align_up(a_bytes, 1024);
   const size_t b_bytes = static_cast<size_t>(NSL) * 4 * d.n * s.kp * 2;
   s.maxa_off = align_up(s.b_off + b_bytes, 256);
-  s.maxb_off = align_up(s.maxa_off + 8 * d.m, 256);
-  s.ea_off = align_up(s.maxb_off + 8 * d.n, 256);
+  s.maxb_off = align_up(s.maxa_off + 4 * d.m, 256);
+  s.ka_off = align_up(s.maxb_off + 4 * d.n, 256);
+  s.kb_off = align_up(s.ka_off + 4 * d.k, 256);
+  s.ea_off = align_up(s.kb_off + 4 * d.k, 256);
   s.eb_off = align_up(s.ea_off + 4 * d.m, 256);
   s.total = align_up(s.eb_off + 4 * d.n, 256);
   return s;
@@ -1022,8 +1061,12 @@ bool encode_slices(CUtensorMap *map, const void *base, int64_t kp, int64_t rows,
   return r == CUDA_SUCCESS;
 }
 
-MaxArgs max_args(const MatView &v, bool by_col, int layout, unsigned long long *out) {
+MaxArgs max_args(const MatView &v, bool by_col, int layout, int *out, int tsign = 0,
+                 const int *ka = nullptr, const int *kb = nullptr) {
   MaxArgs a;
+  a.tsign = tsign;
+  a.ka = ka;
+  a.kb = kb;
   a.X = static_cast<const double *>(v.ptr);
   a.ld = v.ld;
   a.ps = v.ps;
@@ -1037,9 +1080,12 @@ MaxArgs max_args(const MatView &v, bool by_col, int layout, unsigned long long *
 }
 
 SliceArgs slice_args(bool is_b, const MatView &v, int op, int64_t rows, int64_t kq, int64_t kp,
-                     int kw, int layout, __nv_bfloat16 *out, const unsigned long long *maxbits,
-                     int *eout) {
+                     int kw, int layout, __nv_bfloat16 *out, const int *emax, int *eout,
+                     int tsign = 0, const int *ka = nullptr, const int *kb = nullptr) {
   SliceArgs a;
+  a.tsign = tsign;
+  a.ka = ka;
+  a.kb = kb;
   a.X = static_cast<const double *>(v.ptr);
   a.ld = v.ld;
   a.ps = v.ps;
@@ -1048,7 +1094,7 @@ SliceArgs slice_args(bool is_b, const MatView &v, int op, int64_t rows, int64_t 
   a.kp = kp;
   a.slice_stride = (is_b ? 4 * rows : rows) * kp;
   a.out = out;
-  a.maxbits = maxbits;
+  a.emax = emax;
   a.eout = eout;
   a.layout = layout;
   a.row_contig = is_b ? (op_trans(op) ? 1 : 0) : (op_trans(op) ? 0 : 1);
@@ -1185,23 +1231,32 @@ int launch_sliced_gemm(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_
   unsigned char *w = static_cast<unsigned char *>(ws);
   auto *wa = reinterpret_cast<__nv_bfloat16 *>(w + pl.a_off);
   auto *wb = reinterpret_cast<__nv_bfloat16 *>(w + pl.b_off);
-  auto *maxa = reinterpret_cast<unsigned long long *>(w + pl.maxa_off);
-  auto *maxb = reinterpret_cast<unsigned long long *>(w + pl.maxb_off);
+  int *maxa = reinterpret_cast<int *>(w + pl.maxa_off);
+  int *maxb = reinterpret_cast<int *>(w + pl.maxb_off);
+  int *ka = reinterpret_cast<int *>(w + pl.ka_off);
+  int *kb = reinterpret_cast<int *>(w + pl.kb_off);
   int *ea = reinterpret_cast<int *>(w + pl.ea_off);
   int *eb = reinterpret_cast<int *>(w + pl.eb_off);
 
-  if (cudaMemsetAsync(w + pl.maxa_off, 0, pl.ea_off - pl.maxa_off, stream) != cudaSuccess)
+  // every maximum starts at kExpEmpty (bytes 0x80)
+  if (cudaMemsetAsync(w + pl.maxa_off, 0x80, pl.ea_off - pl.maxa_off, stream) != cudaSuccess)
     return launch_status();
-  int rc = launch_max(max_args(d.A, max_by_col(false, d.opA), d.layout, maxa), stream);
+  // per-kappa exponents of op(A) and op(B), then the balanced row / column
+  // exponents, then the balanced slices
+  int rc = launch_max(max_args(d.A, !max_by_col(false, d.opA), d.layout, ka), stream);
   if (rc) return rc;
-  rc = launch_max(max_args(d.B, max_by_col(true, d.opB), d.layout, maxb), stream);
+  rc = launch_max(max_args(d.B, !max_by_col(true, d.opB), d.layout, kb), stream);
+  if (rc) return rc;
+  rc = launch_max(max_args(d.A, max_by_col(false, d.opA), d.layout, maxa, -1, ka, kb), stream);
+  if (rc) return rc;
+  rc = launch_max(max_args(d.B, max_by_col(true, d.opB), d.layout, maxb, 1, ka, kb), stream);
   if (rc) return rc;
   rc = launch_slices(false, slice_args(false, d.A, d.opA, d.m, d.k, pl.kp, d.kwidth, d.layout, wa,
-                                      maxa, ea),
+                                      maxa, ea, -1, ka, kb),
                      stream);
   if (rc) return rc;
   rc = launch_slices(true, slice_args(true, d.B, d.opB, d.n, d.k, pl.kp, d.kwidth, d.layout, wb,
-                                      maxb, eb),
+                                      maxb, eb, 1, ka, kb),
                      stream);
   if (rc) return rc;
 
@@ -1364,8 +1419,8 @@ int prepare_sliced_grouped(const std::vector<GemmDesc> &in, int layout, unsigned
     const int64_t kp = L.kp[p];
     auto *wa = reinterpret_cast<__nv_bfloat16 *>(ws + L.a_off[p]);
     auto *wb = reinterpret_cast<__nv_bfloat16 *>(ws + L.b_off[p]);
-    auto *maxa = reinterpret_cast<unsigned long long *>(ws + L.maxa[p]);
-    auto *maxb = reinterpret_cast<unsigned long long *>(ws + L.maxb[p]);
+    auto *maxa = reinterpret_cast<int *>(ws + L.maxa[p]);
+    auto *maxb = reinterpret_cast<int *>(ws + L.maxb[p]);
     int *ea = reinterpret_cast<int *>(ws + L.ea[p]);
     int *eb = reinterpret_cast<int *>(ws + L.eb[p]);
     GemmDesc dl = d;
@@ -1449,7 +1504,7 @@ int launch_sliced_grouped(const qgemm_grouped_plan *plan, cudaStream_t s) {
   const int nm = static_cast<int>(plan->reserved[1] & 0xffffffff);
   const int ns = static_cast<int>(plan->reserved[1] >> 32);
   if (plan->reserved[3] > 0 &&
-      cudaMemsetAsync(ws + plan->data_offset, 0, static_cast<size_t>(plan->reserved[3]), s) !=
+      cudaMemsetAsync(ws + plan->data_offset, 0x80, static_cast<size_t>(plan->reserved[3]), s) !=
           cudaSuccess)
     return launch_status();
   const int pgrid = plan->reserved0 > 0 ? plan->reserved0 : 1;

@@ -196,6 +196,34 @@ def test_sampled_1024_all_ops(layout):
         _sampled_check(opA, opB, 1024, layout, 3000 + i, nrand=128)
 
 
+@pytest.mark.parametrize("layout", qsynth.LAYOUTS)
+def test_sampled_2048_all_ops(layout):
+    """m = n = k = 2048, every op pair: sampled entries and Freivalds probes."""
+    for i, (opA, opB) in enumerate([(a, b) for a in OPS for b in OPS]):
+        _sampled_check(opA, opB, 2048, layout, 3100 + i, nrand=128)
+
+
+def test_sampled_4096_planes():
+    """m = n = k = 4096 in the split-plane layout (op N,N)."""
+    err = _sampled_check("N", "N", 4096, "planes", 1915)
+    print("4096 planes sampled rel err %.3e" % err)
+
+
+@pytest.mark.parametrize("opA,opB", [("H", "T"), ("C", "N")])
+def test_sampled_4096_other_ops(opA, opB):
+    """m = n = k = 4096 with transposed and conjugated operands."""
+    err = _sampled_check(opA, opB, 4096, "interleaved", 1917 + OPS.index(opA))
+    print("4096 %s,%s sampled rel err %.3e" % (opA, opB, err))
+
+
+@pytest.mark.parametrize("layout", qsynth.LAYOUTS)
+def test_sampled_8192(layout):
+    """m = n = k = 8192 (op N,N), the largest square of the sweep: sampled
+    entries and Freivalds probes (about 16 s on the DMMA path)."""
+    err = _sampled_check("N", "N", 8192, layout, 1921, nrand=256)
+    print("8192 %s sampled rel err %.3e" % (layout, err))
+
+
 def test_sampled_4096_bench_config():
     """The benchmarked launch: m=n=k=4096, op N,N, interleaved, unit alpha/beta."""
     err = _sampled_check("N", "N", 4096, "interleaved", 1905)
