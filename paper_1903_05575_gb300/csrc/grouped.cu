@@ -71,6 +71,20 @@ int default_shape(int64_t m, int64_t n) {
   return 0;
 }
 
+// Split-BF16 batches: column-tile width per size bucket (code 0: 64, 1: 32,
+// 2: 16 quaternion columns), 64 before tuning.
+constexpr int kSplitWidths = 3;
+__host__ __device__ constexpr int split_width(int code) { return code == 1 ? 32 : (code == 2 ? 16 : 64); }
+int g_split_table[kBuckets];
+bool g_split_table_set = false;
+
+int split_width_for(int64_t m, int64_t n) {
+  std::lock_guard<std::mutex> lock(g_table_mu);
+  if (!g_split_table_set) return 64;
+  const int c = g_split_table[bucket_of(m, n)];
+  return split_width(c >= 0 && c < kSplitWidths ? c : 0);
+}
+
 int shape_for(int64_t m, int64_t n) {
   std::lock_guard<std::mutex> lock(g_table_mu);
   if (!g_table_set) return default_shape(m, n);
@@ -242,6 +256,7 @@ struct SplitLayout {
   int64_t tiles, ptiles;
   std::vector<size_t> a_off, b_off;  // per problem, relative to the workspace
   std::vector<int64_t> kp;
+  std::vector<int> width;            // per problem: column-tile width
 };
 
 int64_t split_kp(int64_t k) { return (k + 7) / 8 * 8; }
@@ -286,13 +301,15 @@ SplitLayout layout_split(const std::vector<GemmDesc> &ds_in) {
   L.a_off.resize(ds_in.size());
   L.b_off.resize(ds_in.size());
   L.kp.resize(ds_in.size());
+  L.width.assign(ds_in.size(), 64);
   size_t data = 0;
   for (size_t p = 0; p < ds_in.size(); ++p) {
     bool sw;
     const GemmDesc d = oriented(ds_in[p], &sw);
     L.kp[p] = split_kp(d.k);
     if (d.m == 0 || d.n == 0) continue;
-    tiles += ((d.m + split::BM - 1) / split::BM) * ((d.n + split::BNQ - 1) / split::BNQ);
+    const int64_t w = L.width[p] = split_width_for(d.m, d.n);
+    tiles += ((d.m + split::BM - 1) / split::BM) * ((d.n + w - 1) / w);
     if (d.k > 0) {
       const int64_t kt = (d.k + 31) / 32;
       ptiles += ((d.m + 31) / 32) * kt + ((d.n + 31) / 32) * kt;
@@ -400,7 +417,7 @@ int prepare_split(const std::vector<GemmDesc> &ds_in, int layout, unsigned char 
     q.g.ldc = d.ldc;
     q.g.psC = d.psc;
     q.g.swap = sw ? 1 : 0;
-    double_float4(d.beta, q.g.beta_hi, q.g.beta_lo);
+    split::set_beta_table(q.g, d.beta);
     if (d.k > 0) {
       // alpha: on the left of op(A), or (turned around) conj(alpha) on the
       // right of op(A)^H, the B side: (alpha A B)^H = B^H (A^H conj(alpha))
@@ -424,13 +441,16 @@ int prepare_split(const std::vector<GemmDesc> &ds_in, int layout, unsigned char 
       for (int r = 0; r < (d.n + 31) / 32; ++r)
         for (int c = 0; c < kt; ++c) ptiles.push_back(make_int4(static_cast<int>(p), 1, r, c));
     }
-    if (q.g.num_kb >= (1 << 24)) return QGEMM_ERR_UNSUPPORTED;
+    if (q.g.num_kb >= (1 << 24) || d.n > 0x7fffffff) return QGEMM_ERR_UNSUPPORTED;
+    const int width = L.width[p];
     for (int a = 0; a < q.g.num_mt; ++a)
-      for (int b = 0; b < q.g.num_nt; ++b) {
-        // w: the tile's stages and MMA width, so the kernel needs no parameter
-        // load to start it
-        const int w = q.g.num_kb | (split::tile_ncols(q.g, b) << 24);
-        tiles.push_back(make_int4(static_cast<int>(p), a, b, w));
+      for (int64_t n0 = 0; n0 < d.n; n0 += width) {
+        // (problem, row tile, first column, stages | MMA width << 24): the
+        // kernel needs no parameter load to start the tile
+        const int64_t rem = d.n - n0;
+        const int ncols = rem >= width ? width : static_cast<int>((rem + 15) / 16 * 16);
+        tiles.push_back(make_int4(static_cast<int>(p), a, static_cast<int>(n0),
+                                  q.g.num_kb | (ncols << 24)));
         tile_kb.push_back(q.g.num_kb);
       }
   }
@@ -440,6 +460,7 @@ int prepare_split(const std::vector<GemmDesc> &ds_in, int layout, unsigned char 
   for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<int32_t>(i);
   std::stable_sort(order.begin(), order.end(),
                    [&](int32_t a, int32_t b) { return tile_kb[a] > tile_kb[b]; });
+  if (static_cast<int64_t>(tiles.size()) != L.tiles) return QGEMM_ERR_UNSUPPORTED;
   int4 *ht = reinterpret_cast<int4 *>(host.data() + (L.tile_off - L.desc_off));
   for (size_t i = 0; i < order.size(); ++i) ht[i] = tiles[order[i]];
   int4 *hp = reinterpret_cast<int4 *>(host.data() + (L.ptile_off - L.desc_off));
@@ -641,17 +662,19 @@ int qgemm_batched_grouped(const qgemm_problem *problems, int64_t count, int layo
 }
 
 int qgemm_grouped_set_tile_table(int precision, const int32_t *table, int32_t entries) {
-  if (precision != QGEMM_FP64) return -1;
+  if (precision != QGEMM_FP64 && precision != QGEMM_FP32_SPLIT_BF16) return -1;
   if (table != nullptr && entries != kBuckets) return -3;
+  const bool split = precision == QGEMM_FP32_SPLIT_BF16;
   std::lock_guard<std::mutex> lock(g_table_mu);
   if (table == nullptr) {
-    g_table_set = false;
+    (split ? g_split_table_set : g_table_set) = false;
     return QGEMM_SUCCESS;
   }
+  const int limit = split ? kSplitWidths : kNumShapes;
   for (int i = 0; i < kBuckets; ++i)
-    if (table[i] < 0 || table[i] >= kNumShapes) return -2;
-  std::memcpy(g_table, table, sizeof(g_table));
-  g_table_set = true;
+    if (table[i] < 0 || table[i] >= limit) return -2;
+  std::memcpy(split ? g_split_table : g_table, table, sizeof(g_table));
+  (split ? g_split_table_set : g_table_set) = true;
   return QGEMM_SUCCESS;
 }
 

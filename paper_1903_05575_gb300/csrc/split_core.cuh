@@ -357,6 +357,17 @@ __device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
   return r;
 }
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_neg(uint64_t a) { return a ^ 0x8000000080000000ull; }
 __device__ __forceinline__ void two_sum2(uint64_t a, uint64_t b, uint64_t &s, uint64_t &e) {
   s = f2_add(a, b);
   const uint64_t bp = f2_sub(s, a);
@@ -525,6 +536,13 @@ struct GemmParams {
   float *C;
   int64_t ldc, psC;
   float beta_hi[4], beta_lo[4];  // beta as double-float pairs
+  // beta as packed double-float coefficients of the epilogue: for component
+  // pair (2h, 2h + 1) and C component j, the pair (sign(2h ^ j, j)
+  // beta^(2h ^ j), sign(2h+1 ^ j, j) beta^(2h+1 ^ j)), high words in bhi,
+  // low words in blo; entry [2][0] holds (beta^0, beta^0) for a real beta
+  // (set_beta_table fills them)
+  alignas(8) float bhi[3][4][2];
+  alignas(8) float blo[3][4][2];
   int tri;                // 0 full; 1 lower (row >= col) only; 2 upper; real diagonal
   int swap;               // 1: the kernel computed D = (op(A) op(B))^H; store C = conj(D)^T
   int krange;             // k-range of a tile when op(A) or op(B) is triangular (GemmDesc)
@@ -534,6 +552,27 @@ struct GemmParams {
   int ksplit;             // 0 or 1: no split
   float *part;
 };
+
+// Fills beta_hi / beta_lo and the packed coefficient table from beta.
+inline void set_beta_table(GemmParams &g, const double *beta) {
+  for (int s = 0; s < 4; ++s) {
+    g.beta_hi[s] = static_cast<float>(beta[s]);
+    g.beta_lo[s] = static_cast<float>(beta[s] - static_cast<double>(g.beta_hi[s]));
+  }
+  for (int h = 0; h < 2; ++h)
+    for (int j = 0; j < 4; ++j)
+      for (int w = 0; w < 2; ++w) {
+        const int c = 2 * h + w, sidx = c ^ j;
+        const float sg = basis_sign(sidx, j) < 0 ? -1.f : 1.f;
+        g.bhi[h][j][w] = sg * g.beta_hi[sidx];
+        g.blo[h][j][w] = sg * g.beta_lo[sidx];
+      }
+  for (int j = 0; j < 4; ++j)
+    for (int w = 0; w < 2; ++w) {
+      g.bhi[2][j][w] = g.beta_hi[0];
+      g.blo[2][j][w] = g.beta_lo[0];
+    }
+}
 
 // Stages [lo, hi) of tile (mt, nt), share z: all of K, or the part where a
 // triangular operand can be nonzero for the tile's rows or columns; then
@@ -652,14 +691,16 @@ __device__ __forceinline__ void tile_of(int t, const GemmParams &single, const C
   }
 }
 
-// Everything a role needs to know about tile t.  Grouped tiles carry their
-// stage count and MMA width in the tile entry (w = stages | width << 24) and
-// are plain quaternion products, so no role waits on the problem's
-// parameters in global memory before it can start the tile.
+// Everything a role needs to know about tile t.  Grouped tiles are entries
+// (problem, row tile, first column, stages | MMA width << 24): a problem's
+// column tiles are 64, 32 or 16 columns wide (per size bucket), and no role
+// waits on the problem's parameters in global memory before it can start
+// the tile; they are plain quaternion products.
 struct TileInfo {
   const GemmParams *g;
   const CUtensorMap *mA, *mB;
   int mt, nt, z;
+  int n0;            // first quaternion column of the tile
   int kb_lo, kb_hi;  // stages of the tile (its share when K is split)
   int ncols;         // MMA width: valid quaternion columns rounded up to 16
   int pa, pb;        // planes of the A and B operands
@@ -677,7 +718,8 @@ __device__ __forceinline__ TileInfo tile_info(int t, int4 e, const GemmParams &s
     ti.mA = &pr->tmA;
     ti.mB = &pr->tmB;
     ti.mt = e.y;
-    ti.nt = e.z;
+    ti.nt = 0;
+    ti.n0 = e.z;
     ti.z = 0;
     ti.kb_lo = 0;
     ti.kb_hi = e.w & 0xFFFFFF;
@@ -689,6 +731,7 @@ __device__ __forceinline__ TileInfo tile_info(int t, int4 e, const GemmParams &s
     ti.skip = tile_skip(single, ti.mt, ti.nt);
     kb_range(single, ti.mt, ti.nt, ti.z, ti.kb_lo, ti.kb_hi);
     ti.ncols = tile_ncols(single, ti.nt);
+    ti.n0 = ti.nt * BNQ;
     ti.pa = single.pa;
     ti.pb = single.pb;
   }
@@ -702,15 +745,16 @@ __device__ __forceinline__ float *c_elem(const GemmParams &g, int64_t ci, int64_
 }
 
 // Prefetches into L2 the C elements that epilogue() will read for row i and
-// the 32 quaternion columns from nbase (only those inside C).  Issued when a
-// tile starts, so the epilogue's reads of C hit L2 instead of waiting on DRAM
-// one element after another.
-__device__ __forceinline__ void prefetch_c(const GemmParams &g, int64_t i, int64_t nbase) {
+// the 32 quaternion columns from nbase (only those inside C).  Issued two
+// chunks before the tile's last, so the epilogue's reads of C hit L2 instead
+// of waiting on DRAM one element after another.
+__device__ __forceinline__ void prefetch_c(const GemmParams &g, int64_t i, int64_t nbase,
+                                           int64_t nlim) {
   if (g.beta_zero || i >= g.m) return;
 #pragma unroll 4
   for (int q = 0; q < 32; ++q) {
     const int64_t nn = nbase + q;
-    if (nn >= g.n) break;
+    if (nn >= nlim) break;
     const int64_t ci = g.swap ? nn : i, cj = g.swap ? i : nn;
     const float *e = c_elem(g, ci, cj);
     asm volatile("prefetch.global.L2 [%0];" ::"l"(e));
@@ -728,37 +772,67 @@ __device__ __forceinline__ float acc_at(const uint64_t (&acc)[64], int c, int q)
 struct PBatch {
   float p[kCBatch][4];  // P of kCBatch consecutive columns, components 0..3
 };
+struct CBatch {
+  float c[kCBatch][4];  // C of the same columns (zeros where not read)
+};
 
-// out = P + beta C for kCBatch columns from n0 of row i.  Not inlined: one
-// copy of this code serves the tile's eight batches, which keeps the
-// kernel's instruction working set small (small grouped tiles run the
-// epilogue often, and an unrolled copy evicted the hot loops from the
-// instruction cache).
-static __device__ __noinline__ void epilogue_batch(const GemmParams &g, int64_t i, int64_t n0,
-                                            PBatch pb) {
-  float cin[kCBatch][4];
+// Prefetches into L1 the C elements of kCBatch columns from n0 of row i.
+__device__ __forceinline__ void prefetch_c_l1(const GemmParams &g, int64_t i, int64_t n0,
+                                              int64_t nlim) {
+  if (g.beta_zero) return;
+#pragma unroll
+  for (int u = 0; u < kCBatch; ++u) {
+    const int64_t nn = n0 + u;
+    if (nn >= nlim) break;
+    const int64_t ci = g.swap ? nn : i, cj = g.swap ? i : nn;
+    const float *e = c_elem(g, ci, cj);
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(e));
+    if (g.layout != QGEMM_INTERLEAVED) {
+#pragma unroll
+      for (int s = 1; s < 4; ++s) asm volatile("prefetch.global.L1 [%0];" ::"l"(e + s * g.psC));
+    }
+  }
+}
+
+// C of kCBatch columns from n0 of row i (zeros past n or when beta = 0).
+__device__ __forceinline__ void load_c_batch(const GemmParams &g, int64_t i, int64_t n0,
+                                             int64_t nlim, CBatch &cb) {
 #pragma unroll
   for (int u = 0; u < kCBatch; ++u) {
     const int64_t nn = n0 + u;
 #pragma unroll
-    for (int s = 0; s < 4; ++s) cin[u][s] = 0.f;
-    if (g.beta_zero || nn >= g.n) continue;
+    for (int s = 0; s < 4; ++s) cb.c[u][s] = 0.f;
+    if (g.beta_zero || nn >= nlim) continue;
     // element (ci, cj) of C; a transposed problem holds (AB)^H: take conj(D)^T
     const int64_t ci = g.swap ? nn : i, cj = g.swap ? i : nn;
     const float *src = c_elem(g, ci, cj);
     if (g.layout == QGEMM_INTERLEAVED && g.c_vec4) {
       const float4 c4 = *reinterpret_cast<const float4 *>(src);
-      cin[u][0] = c4.x; cin[u][1] = c4.y; cin[u][2] = c4.z; cin[u][3] = c4.w;
+      cb.c[u][0] = c4.x; cb.c[u][1] = c4.y; cb.c[u][2] = c4.z; cb.c[u][3] = c4.w;
     } else {
       const int64_t step = g.layout == QGEMM_INTERLEAVED ? 1 : g.psC;
 #pragma unroll
-      for (int s = 0; s < 4; ++s) cin[u][s] = src[s * step];
+      for (int s = 0; s < 4; ++s) cb.c[u][s] = src[s * step];
     }
   }
+}
+
+// out = P + beta C for kCBatch columns from n0 of row i, in double-float with
+// one rounding: every product of a beta component (hi + lo) and a C
+// component is formed without error (FMA) and summed by TwoSum, on packed
+// component pairs (.f32x2).  Not inlined: one copy of this code serves the
+// tile's eight batches, which keeps the kernel's instruction working set
+// small (small grouped tiles run the epilogue often, and an unrolled copy
+// evicted the hot loops from the instruction cache).
+static __device__ __noinline__ void epilogue_batch(const GemmParams &g, int64_t i, int64_t n0,
+                                                   int64_t nlim, PBatch pb, CBatch cb) {
+  // packed coefficients, precomputed per problem (GemmParams::bhi / blo)
+  const uint64_t *chi = reinterpret_cast<const uint64_t *>(&g.bhi[0][0][0]);
+  const uint64_t *clo = reinterpret_cast<const uint64_t *>(&g.blo[0][0][0]);
 #pragma unroll
   for (int u = 0; u < kCBatch; ++u) {
     const int64_t nn = n0 + u;
-    if (nn >= g.n) continue;
+    if (nn >= nlim) continue;
     if ((g.tri == 1 && i < nn) || (g.tri == 2 && i > nn)) continue;
     float P[4] = {pb.p[u][0], pb.p[u][1], pb.p[u][2], pb.p[u][3]};
     const int64_t ci = g.swap ? nn : i, cj = g.swap ? i : nn;
@@ -769,22 +843,32 @@ static __device__ __noinline__ void epilogue_batch(const GemmParams &g, int64_t 
     }
     float out[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      float hi = P[c], lo = 0.f;
+    for (int h = 0; h < 2; ++h) {
+      uint64_t hi = pack2(__float_as_uint(P[2 * h]), __float_as_uint(P[2 * h + 1])), lo = 0ull;
+      auto add_term = [&](uint64_t kh, uint64_t kl, uint64_t x) {
+        const uint64_t p = f2_mul(kh, x);
+        uint64_t e = f2_fma(kh, x, f2_neg(p));
+        e = f2_fma(kl, x, e);
+        uint64_t s2, e2;
+        two_sum2(hi, p, s2, e2);
+        hi = s2;
+        lo = f2_add(lo, f2_add(e, e2));
+      };
       if (!g.beta_zero) {
         if (g.beta_real) {
-          df_fma(hi, lo, g.beta_hi[0], g.beta_lo[0], cin[u][c]);
+          add_term(chi[8], clo[8], pack2(__float_as_uint(cb.c[u][2 * h]),
+                                         __float_as_uint(cb.c[u][2 * h + 1])));
         } else {
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            const int s = c ^ j;  // the sign is a compile-time constant here
-            const bool neg = basis_sign(s, j) < 0;
-            df_fma(hi, lo, neg ? -g.beta_hi[s] : g.beta_hi[s], neg ? -g.beta_lo[s] : g.beta_lo[s],
-                   cin[u][j]);
+            const uint32_t cj32 = __float_as_uint(cb.c[u][j]);
+            add_term(chi[4 * h + j], clo[4 * h + j], pack2(cj32, cj32));
           }
         }
       }
-      out[c] = __fadd_rn(hi, lo);
+      const uint64_t r = f2_add(hi, lo);
+      out[2 * h] = lo_of(r);
+      out[2 * h + 1] = hi_of(r);
     }
     if (g.tri && i == nn) out[1] = out[2] = out[3] = 0.f;  // Hermitian diagonal is real
     float *dst0 = c_elem(g, ci, cj);
@@ -801,23 +885,27 @@ static __device__ __noinline__ void epilogue_batch(const GemmParams &g, int64_t 
   }
 }
 
-// Epilogue of one tile for one drain thread: row i, 32 quaternion columns
-// starting at nbase, accumulated P in packed pairs (component c of column q
+// Epilogue of one tile for one drain thread: row i, the quaternion columns
+// from nbase up to 32 or the tile's end nlim, accumulated P in packed pairs (component c of column q
 // is word q % 2 of acc[16 c + q / 2]); out = P + beta C (beta on the left)
 // in double-float with one rounding, kCBatch columns per call.
 __device__ __forceinline__ void epilogue(const GemmParams &g, int64_t i, int64_t nbase,
-                                         const uint64_t (&acc)[64]) {
+                                         int64_t nlim, const uint64_t (&acc)[64]) {
   if (i >= g.m) return;
   if (g.tri == 2 && nbase + 31 < i) return;
 #pragma unroll
   for (int qb = 0; qb < 32; qb += kCBatch) {
-    if (nbase + qb >= g.n) break;
+    if (nbase + qb >= nlim) break;
+    // the next batch's C moves into L1 while this batch computes
+    if (qb + kCBatch < 32) prefetch_c_l1(g, i, nbase + qb + kCBatch, nlim);
+    CBatch cur;
+    load_c_batch(g, i, nbase + qb, nlim, cur);
     PBatch pb;
 #pragma unroll
     for (int u = 0; u < kCBatch; ++u)
 #pragma unroll
       for (int c = 0; c < 4; ++c) pb.p[u][c] = acc_at(acc, c, qb + u);
-    epilogue_batch(g, i, nbase + qb, pb);
+    epilogue_batch(g, i, nbase + qb, nlim, pb, cur);
   }
 }
 
@@ -997,7 +1085,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const TileInfo ti = tile_info<GROUPED>(t, e, single, &tmA, &tmB, probs);
         if (ti.skip) continue;
         const CUtensorMap *mA = ti.mA, *mB = ti.mB;
-        const int mt = ti.mt, nt = ti.nt;
+        const int mt = ti.mt, n0 = ti.n0;
         const uint32_t bytes = static_cast<uint32_t>(ti.pa) * TERMS * kAPlaneBytes +
                                static_cast<uint32_t>(ti.pb) * TERMS * kBPlaneBytes;
         for (int kb = ti.kb_lo; kb < ti.kb_hi; ++kb, ++s_run) {
@@ -1011,7 +1099,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           unsigned char *sa = ring + st * kStageBytes;
           mbar_arrive_expect_tx(&ctl->full[st], bytes);
           tma_load_4d(sa, mA, &ctl->full[st], kb * KQ, mt * BM, 0, 0);
-          tma_load_4d(sa + kStageA, mB, &ctl->full[st], kb * KQ, nt * BNQ, 0, 0);
+          tma_load_4d(sa + kStageA, mB, &ctl->full[st], kb * KQ, n0, 0, 0);
         }
       }
       producer = true;
@@ -1085,19 +1173,26 @@ __global__ void __launch_bounds__(kThreads, 1)
       const TileInfo ti = tile_info<GROUPED>(t, e, single, &tmA, &tmB, probs);
       if (ti.skip) continue;
       const GemmParams *g = ti.g;
-      const int mt = ti.mt, nt = ti.nt, z = ti.z;
+      const int mt = ti.mt, z = ti.z;
+      // this thread's columns: from nbase to the tile's end nlim
+      const int64_t nbase = static_cast<int64_t>(ti.n0) + 32 * half;
+      const int64_t nlim = min(g->n, static_cast<int64_t>(ti.n0) + ti.ncols);
       const int nch = (ti.kb_hi - ti.kb_lo + kChunk - 1) / kChunk;
       const bool mine = 32 * half < ti.ncols;          // this warp's columns hold data
       const int nacc = ti.pa > ti.pb ? ti.pa : ti.pb;  // components the MMAs write
       const bool split_k = !GROUPED && single.ksplit > 1;  // grouped problems never split K
-      if (!split_k && mine)
-        prefetch_c(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane,
-                   static_cast<int64_t>(nt) * BNQ + 32 * half);
+      // C moves into L2 two chunks before the epilogue reads it (earlier, the
+      // streaming operands of the other tiles evict it again)
+      const int pf_chunk = nch > 2 ? nch - 2 : 0;
+      if (!split_k && mine && nch == 0)
+        prefetch_c(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane, nbase, nlim);
       uint64_t acc[64];  // packed pairs: component c, columns 2i, 2i + 1 in acc[16 c + i]
 #pragma unroll
       for (int i = 0; i < 64; ++i) acc[i] = 0ull;
       for (int ch = 0; ch < nch; ++ch, ++c_run) {
         const int b = c_run & 1;
+        if (ch == pf_chunk && !split_k && mine)
+          prefetch_c(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane, nbase, nlim);
         if (!wait_phase(&ctl->accfull[b], (c_run >> 1) & 1, limit_ns, ctl)) {
           set_abort<Err>(ctl);
           ok = false;
@@ -1143,11 +1238,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) break;
       if (!mine) continue;
       if (split_k)
-        store_partial(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane,
-                      static_cast<int64_t>(nt) * BNQ + 32 * half, z, acc);
+        store_partial(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane, nbase, z, acc);
       else
-        epilogue(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane,
-                 static_cast<int64_t>(nt) * BNQ + 32 * half, acc);
+        epilogue(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane, nbase, nlim, acc);
     }
   }
 

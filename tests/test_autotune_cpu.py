@@ -34,3 +34,37 @@ def test_plan_applied_only_for_matching_key(tmp_path):
     path.write_text(json.dumps(dict(plan, table=[1] * 24)))
     assert autotune.load_plan(str(path), key=key, install=False) is None
     assert autotune.load_plan(str(tmp_path / "missing.json"), key=key, install=False) is None
+
+
+def test_split_width_table_sets_the_tile_count():
+    """Split-BF16 batches: the per-bucket column-tile width (codes 0, 1, 2 for
+    64, 32, 16 columns) is installed by qgemm_grouped_set_tile_table and
+    decides how many tiles (16-byte entries) a problem's schedule has."""
+    import ctypes
+
+    from paper_1903_05575_gb300 import _abi
+    L = _abi.lib()
+    count = 32
+    arr = (_abi.QgemmProblem * count)()
+    for q in arr:
+        q.opA = q.opB = 0
+        q.m, q.n, q.k = 100, 200, 40   # bucket (65-128, 129-256), computed as it is
+        q.alpha[0] = 1.0
+        q.A = q.B = q.C = 64
+        q.lda, q.ldb, q.ldc = 100, 40, 100
+
+    def ws_with(code):
+        tbl = (ctypes.c_int32 * 25)(*([code] * 25))
+        assert L.qgemm_grouped_set_tile_table(_abi.PRECISION["split_bf16"], tbl, 25) == 0
+        return L.qgemm_grouped_workspace_bytes(arr, count, 0, _abi.PRECISION["split_bf16"])
+    try:
+        sizes = [ws_with(c) for c in range(3)]
+        bad = (ctypes.c_int32 * 25)(*([3] * 25))
+        assert L.qgemm_grouped_set_tile_table(_abi.PRECISION["split_bf16"], bad, 25) == -2
+    finally:
+        assert L.qgemm_grouped_set_tile_table(_abi.PRECISION["split_bf16"], None, 0) == 0
+    # 1 row tile x ceil(200 / w) column tiles, 16 bytes each (up to 256-byte rounding)
+    tiles = [-(-200 // w) for w in autotune.SPLIT_WIDTHS]
+    assert tiles == [4, 7, 13]
+    assert sizes[0] < sizes[1] < sizes[2]
+    assert abs((sizes[2] - sizes[0]) - 16 * count * (tiles[2] - tiles[0])) <= 512
