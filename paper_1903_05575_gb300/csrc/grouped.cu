@@ -417,7 +417,7 @@ int prepare_split(const std::vector<GemmDesc> &ds_in, int layout, unsigned char 
     q.g.ldc = d.ldc;
     q.g.psC = d.psc;
     q.g.swap = sw ? 1 : 0;
-    split::set_beta_table(q.g, d.beta);
+    split::set_beta(q.g, d.beta);
     if (d.k > 0) {
       // alpha: on the left of op(A), or (turned around) conj(alpha) on the
       // right of op(A)^H, the B side: (alpha A B)^H = B^H (A^H conj(alpha))

@@ -457,7 +457,7 @@ GemmParams gemm_params(const GemmDesc &d, const SplitPlan &pl) {
   g.krange = d.krange;
   g.swap = d.swap;
   g.c_vec4 = (reinterpret_cast<uintptr_t>(d.C) % 16 == 0) ? 1 : 0;
-  set_beta_table(g, d.beta);
+  set_beta(g, d.beta);
   return g;
 }
 

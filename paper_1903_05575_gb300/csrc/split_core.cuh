@@ -20,8 +20,10 @@
 // Scalars.  alpha is applied to op(A) by the pre-pass, in double-float
 // arithmetic (pairs of FP32 with error-free products and sums), before the
 // split: (alpha op(A)) op(B) = alpha (op(A) op(B)) (associativity; the
-// scalar acts from the left, Sec. 2.2).  beta C is added by the epilogue in
-// the same arithmetic, with one final rounding.
+// scalar acts from the left, Sec. 2.2).  beta C (FP32 products) is where a
+// tile's accumulation starts: C is read at the start of the tile, while its
+// first MMAs run, and enters the compensated sum below like one more chunk,
+// so the end of a tile only stores.
 //
 // Precision.  Each value x (an FP32 input, or alpha x in double-float) is
 // split by round-to-nearest into three BF16 terms hi + mid + lo, with a
@@ -40,8 +42,8 @@
 // warp issues TMA loads (4-D boxes: kappa x rows x planes x terms, 32-byte
 // swizzle) into a 3-stage ring, one warp issues the MMAs (M = 128, N <= 64,
 // K = 16) into one of two TMEM accumulator sets and commits them to
-// mbarriers, eight warps drain TMEM and run the epilogue of a tile while the
-// MMAs of the next one proceed.  Ring slots, barrier phases and TMEM buffers
+// mbarriers, eight warps drain TMEM and store a tile while the MMAs of the
+// next one proceed.  Ring slots, barrier phases and TMEM buffers
 // are indexed by running counters that continue across tiles.  Every wait is
 // bounded.
 #pragma once
@@ -535,14 +537,7 @@ struct GemmParams {
   int c_vec4;             // interleaved C 16-byte aligned: float4 access
   float *C;
   int64_t ldc, psC;
-  float beta_hi[4], beta_lo[4];  // beta as double-float pairs
-  // beta as packed double-float coefficients of the epilogue: for component
-  // pair (2h, 2h + 1) and C component j, the pair (sign(2h ^ j, j)
-  // beta^(2h ^ j), sign(2h+1 ^ j, j) beta^(2h+1 ^ j)), high words in bhi,
-  // low words in blo; entry [2][0] holds (beta^0, beta^0) for a real beta
-  // (set_beta_table fills them)
-  alignas(8) float bhi[3][4][2];
-  alignas(8) float blo[3][4][2];
+  float beta_f[4];         // beta rounded to FP32 (beta C is formed in FP32)
   int tri;                // 0 full; 1 lower (row >= col) only; 2 upper; real diagonal
   int swap;               // 1: the kernel computed D = (op(A) op(B))^H; store C = conj(D)^T
   int krange;             // k-range of a tile when op(A) or op(B) is triangular (GemmDesc)
@@ -553,25 +548,9 @@ struct GemmParams {
   float *part;
 };
 
-// Fills beta_hi / beta_lo and the packed coefficient table from beta.
-inline void set_beta_table(GemmParams &g, const double *beta) {
-  for (int s = 0; s < 4; ++s) {
-    g.beta_hi[s] = static_cast<float>(beta[s]);
-    g.beta_lo[s] = static_cast<float>(beta[s] - static_cast<double>(g.beta_hi[s]));
-  }
-  for (int h = 0; h < 2; ++h)
-    for (int j = 0; j < 4; ++j)
-      for (int w = 0; w < 2; ++w) {
-        const int c = 2 * h + w, sidx = c ^ j;
-        const float sg = basis_sign(sidx, j) < 0 ? -1.f : 1.f;
-        g.bhi[h][j][w] = sg * g.beta_hi[sidx];
-        g.blo[h][j][w] = sg * g.beta_lo[sidx];
-      }
-  for (int j = 0; j < 4; ++j)
-    for (int w = 0; w < 2; ++w) {
-      g.bhi[2][j][w] = g.beta_hi[0];
-      g.blo[2][j][w] = g.beta_lo[0];
-    }
+// Sets beta_f from beta.
+inline void set_beta(GemmParams &g, const double *beta) {
+  for (int s = 0; s < 4; ++s) g.beta_f[s] = static_cast<float>(beta[s]);
 }
 
 // Stages [lo, hi) of tile (mt, nt), share z: all of K, or the part where a
@@ -738,174 +717,178 @@ __device__ __forceinline__ TileInfo tile_info(int t, int4 e, const GemmParams &s
   return ti;
 }
 
-// Address of element (ci, cj) of C: the first component (interleaved) or the
-// component-0 plane entry (planes).
-__device__ __forceinline__ float *c_elem(const GemmParams &g, int64_t ci, int64_t cj) {
-  return g.layout == QGEMM_INTERLEAVED ? g.C + 4 * (ci + cj * g.ldc) : g.C + ci + cj * g.ldc;
+// One drain thread's share of a tile's C: row i of the tile's orientation and
+// the nq quaternion columns from nbase.  Element (i, nbase + q) of the tile
+// sits at base + q step with its components cs apart (a transposed problem
+// walks a row of C instead of a column).  Read from the problem's parameters
+// once per tile and kept in registers: the stores to C then never make the
+// compiler re-read the parameters (it cannot prove that they differ).
+struct CRow {
+  float *base;
+  int64_t i, nbase, step, cs;
+  int nq;         // 0: no element of this thread inside C
+  int vec4;       // interleaved, 16-byte aligned: one float4 per element
+  int swap, tri;
+  int beta_mode;  // 0: beta C not added here (beta = 0, or K split); 1 real beta; 2 general
+  float beta[4];
+};
+
+__device__ __forceinline__ CRow c_row(const GemmParams &g, int64_t i, int64_t nbase, int64_t nlim,
+                                      bool with_beta) {
+  CRow r;
+  const bool il = g.layout == QGEMM_INTERLEAVED;
+  const int64_t w = il ? 4 : 1;
+  r.i = i;
+  r.nbase = nbase;
+  r.nq = (i < g.m && nbase < nlim) ? static_cast<int>(min(static_cast<int64_t>(32), nlim - nbase))
+                                   : 0;
+  r.swap = g.swap;
+  r.tri = g.tri;
+  // element (ci, cj) of C is at C + w (ci + cj ldc); transposed: (ci, cj) = (nn, i)
+  r.base = r.nq == 0 ? g.C : g.C + (g.swap ? w * (nbase + i * g.ldc) : w * (i + nbase * g.ldc));
+  r.step = g.swap ? w : w * g.ldc;
+  r.cs = il ? 1 : g.psC;
+  r.vec4 = il && g.c_vec4;
+  r.beta_mode = (!with_beta || g.beta_zero) ? 0 : g.beta_real ? 1 : 2;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) r.beta[s] = g.beta_f[s];
+  return r;
 }
 
-// Prefetches into L2 the C elements that epilogue() will read for row i and
-// the 32 quaternion columns from nbase (only those inside C).  Issued two
-// chunks before the tile's last, so the epilogue's reads of C hit L2 instead
-// of waiting on DRAM one element after another.
-__device__ __forceinline__ void prefetch_c(const GemmParams &g, int64_t i, int64_t nbase,
-                                           int64_t nlim) {
-  if (g.beta_zero || i >= g.m) return;
-#pragma unroll 4
-  for (int q = 0; q < 32; ++q) {
-    const int64_t nn = nbase + q;
-    if (nn >= nlim) break;
-    const int64_t ci = g.swap ? nn : i, cj = g.swap ? i : nn;
-    const float *e = c_elem(g, ci, cj);
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(e));
-    if (g.layout != QGEMM_INTERLEAVED) {
+// C columns of the next tile that a drain thread loads before it stores the
+// current tile, so that their latency passes while the stores go out.
+constexpr int kCPre = 8;
+
+// C of columns [q0, q0 + NQ) of r (zeros outside C, and when beta C is not
+// added here).  The loads bypass L1: its few KB beside the operand ring would
+// hold only a handful of them in flight.
+template <int NQ>
+__device__ __forceinline__ void load_c(const CRow &r, int q0, float4 (&cv)[NQ]) {
 #pragma unroll
-      for (int s = 1; s < 4; ++s) asm volatile("prefetch.global.L2 [%0];" ::"l"(e + s * g.psC));
+  for (int u = 0; u < NQ; ++u) {
+    cv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r.beta_mode == 0 || q0 + u >= r.nq) continue;
+    const float *e = r.base + (q0 + u) * r.step;
+    if (r.vec4)
+      cv[u] = __ldcg(reinterpret_cast<const float4 *>(e));
+    else
+      cv[u] = make_float4(__ldcg(e), __ldcg(e + r.cs), __ldcg(e + 2 * r.cs), __ldcg(e + 3 * r.cs));
+  }
+}
+
+// acc <- beta C for columns [q0, q0 + NQ) (q0, NQ even) from their C values:
+// beta on the left, FP32 products, two columns per packed (.f32x2) FMA.  A
+// transposed problem accumulates D = (op(A) op(B))^H and stores conj(D), so
+// it starts from conj(beta C).
+template <int NQ>
+__device__ __forceinline__ void beta_c_into(const CRow &r, int q0, const float4 (&cv)[NQ],
+                                            uint64_t (&acc)[64]) {
+  // coefficient of C^j in component c: sign(e_{c^j} e_j) beta^{c^j} (a real
+  // beta: beta^0 on the diagonal only), times -1 for c > 0 when conjugated
+  float k[4][4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float b = r.beta_mode == 1 ? (c == j ? r.beta[0] : 0.f)
+                                       : (basis_sign(c ^ j, j) < 0 ? -r.beta[c ^ j] : r.beta[c ^ j]);
+      k[c][j] = (c > 0 && r.swap) ? -b : b;
+    }
+#pragma unroll
+  for (int u = 0; u < NQ; u += 2) {
+    const uint64_t x[4] = {pack2(__float_as_uint(cv[u].x), __float_as_uint(cv[u + 1].x)),
+                           pack2(__float_as_uint(cv[u].y), __float_as_uint(cv[u + 1].y)),
+                           pack2(__float_as_uint(cv[u].z), __float_as_uint(cv[u + 1].z)),
+                           pack2(__float_as_uint(cv[u].w), __float_as_uint(cv[u + 1].w))};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      uint64_t v = 0ull;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t kj = __float_as_uint(k[c][j]);
+        v = f2_fma(pack2(kj, kj), x[j], v);
+      }
+      acc[16 * c + ((q0 + u) >> 1)] = v;
     }
   }
 }
 
-constexpr int kCBatch = 4;
+// Starts the accumulation of a tile at beta C (zero where C is not read), so
+// that C enters the compensated sum like one more chunk and the tile's end
+// only stores.  pre holds the first kCPre columns when have_pre (loaded
+// before the previous tile's stores); the other loads are all issued before
+// their first use and wait on memory while the tile's first chunk runs on
+// the tensor cores.
+__device__ __forceinline__ void acc_init_beta_c(const CRow &r, uint64_t (&acc)[64],
+                                                const float4 (&pre)[kCPre], bool have_pre) {
+  if (r.beta_mode == 0) {
+#pragma unroll
+    for (int i = 0; i < 64; ++i) acc[i] = 0ull;
+    return;
+  }
+  if (have_pre) {
+    beta_c_into<kCPre>(r, 0, pre, acc);
+  } else {
+    float4 first[kCPre];
+    load_c<kCPre>(r, 0, first);
+    beta_c_into<kCPre>(r, 0, first, acc);
+  }
+  constexpr int kHalf = (32 - kCPre) / 2;
+  float4 rest[kHalf];
+  load_c<kHalf>(r, kCPre, rest);
+  beta_c_into<kHalf>(r, kCPre, rest, acc);
+  load_c<kHalf>(r, kCPre + kHalf, rest);
+  beta_c_into<kHalf>(r, kCPre + kHalf, rest, acc);
+}
+
 __device__ __forceinline__ float acc_at(const uint64_t (&acc)[64], int c, int q) {
   return (q & 1) ? hi_of(acc[16 * c + (q >> 1)]) : lo_of(acc[16 * c + (q >> 1)]);
 }
-struct PBatch {
-  float p[kCBatch][4];  // P of kCBatch consecutive columns, components 0..3
-};
-struct CBatch {
-  float c[kCBatch][4];  // C of the same columns (zeros where not read)
-};
 
-// Prefetches into L1 the C elements of kCBatch columns from n0 of row i.
-__device__ __forceinline__ void prefetch_c_l1(const GemmParams &g, int64_t i, int64_t n0,
-                                              int64_t nlim) {
-  if (g.beta_zero) return;
+// Stores the accumulated tile (alpha op(A) op(B) + beta C, or its conjugate
+// for a transposed problem) for this thread's row and columns [Q0, Q1): only
+// the stored triangle when the problem is a Hermitian update, whose diagonal
+// is real.
+template <int Q0, int Q1>
+__device__ __forceinline__ void store_acc(const CRow &r, const uint64_t (&acc)[64]) {
 #pragma unroll
-  for (int u = 0; u < kCBatch; ++u) {
-    const int64_t nn = n0 + u;
-    if (nn >= nlim) break;
-    const int64_t ci = g.swap ? nn : i, cj = g.swap ? i : nn;
-    const float *e = c_elem(g, ci, cj);
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(e));
-    if (g.layout != QGEMM_INTERLEAVED) {
+  for (int q = Q0; q < Q1; ++q) {
+    if (q >= r.nq) break;
+    const int64_t nn = r.nbase + q;
+    if ((r.tri == 1 && r.i < nn) || (r.tri == 2 && r.i > nn)) continue;
+    float o[4];
 #pragma unroll
-      for (int s = 1; s < 4; ++s) asm volatile("prefetch.global.L1 [%0];" ::"l"(e + s * g.psC));
+    for (int c = 0; c < 4; ++c) o[c] = acc_at(acc, c, q);
+    if (r.swap) {
+      o[1] = -o[1];
+      o[2] = -o[2];
+      o[3] = -o[3];
     }
-  }
-}
-
-// C of kCBatch columns from n0 of row i (zeros past n or when beta = 0).
-__device__ __forceinline__ void load_c_batch(const GemmParams &g, int64_t i, int64_t n0,
-                                             int64_t nlim, CBatch &cb) {
-#pragma unroll
-  for (int u = 0; u < kCBatch; ++u) {
-    const int64_t nn = n0 + u;
-#pragma unroll
-    for (int s = 0; s < 4; ++s) cb.c[u][s] = 0.f;
-    if (g.beta_zero || nn >= nlim) continue;
-    // element (ci, cj) of C; a transposed problem holds (AB)^H: take conj(D)^T
-    const int64_t ci = g.swap ? nn : i, cj = g.swap ? i : nn;
-    const float *src = c_elem(g, ci, cj);
-    if (g.layout == QGEMM_INTERLEAVED && g.c_vec4) {
-      const float4 c4 = *reinterpret_cast<const float4 *>(src);
-      cb.c[u][0] = c4.x; cb.c[u][1] = c4.y; cb.c[u][2] = c4.z; cb.c[u][3] = c4.w;
-    } else {
-      const int64_t step = g.layout == QGEMM_INTERLEAVED ? 1 : g.psC;
-#pragma unroll
-      for (int s = 0; s < 4; ++s) cb.c[u][s] = src[s * step];
-    }
-  }
-}
-
-// out = P + beta C for kCBatch columns from n0 of row i, in double-float with
-// one rounding: every product of a beta component (hi + lo) and a C
-// component is formed without error (FMA) and summed by TwoSum, on packed
-// component pairs (.f32x2).  Not inlined: one copy of this code serves the
-// tile's eight batches, which keeps the kernel's instruction working set
-// small (small grouped tiles run the epilogue often, and an unrolled copy
-// evicted the hot loops from the instruction cache).
-static __device__ __noinline__ void epilogue_batch(const GemmParams &g, int64_t i, int64_t n0,
-                                                   int64_t nlim, PBatch pb, CBatch cb) {
-  // packed coefficients, precomputed per problem (GemmParams::bhi / blo)
-  const uint64_t *chi = reinterpret_cast<const uint64_t *>(&g.bhi[0][0][0]);
-  const uint64_t *clo = reinterpret_cast<const uint64_t *>(&g.blo[0][0][0]);
-#pragma unroll
-  for (int u = 0; u < kCBatch; ++u) {
-    const int64_t nn = n0 + u;
-    if (nn >= nlim) continue;
-    if ((g.tri == 1 && i < nn) || (g.tri == 2 && i > nn)) continue;
-    float P[4] = {pb.p[u][0], pb.p[u][1], pb.p[u][2], pb.p[u][3]};
-    const int64_t ci = g.swap ? nn : i, cj = g.swap ? i : nn;
-    if (g.swap) {
-      P[1] = -P[1];
-      P[2] = -P[2];
-      P[3] = -P[3];
-    }
-    float out[4];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      uint64_t hi = pack2(__float_as_uint(P[2 * h]), __float_as_uint(P[2 * h + 1])), lo = 0ull;
-      auto add_term = [&](uint64_t kh, uint64_t kl, uint64_t x) {
-        const uint64_t p = f2_mul(kh, x);
-        uint64_t e = f2_fma(kh, x, f2_neg(p));
-        e = f2_fma(kl, x, e);
-        uint64_t s2, e2;
-        two_sum2(hi, p, s2, e2);
-        hi = s2;
-        lo = f2_add(lo, f2_add(e, e2));
-      };
-      if (!g.beta_zero) {
-        if (g.beta_real) {
-          add_term(chi[8], clo[8], pack2(__float_as_uint(cb.c[u][2 * h]),
-                                         __float_as_uint(cb.c[u][2 * h + 1])));
-        } else {
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const uint32_t cj32 = __float_as_uint(cb.c[u][j]);
-            add_term(chi[4 * h + j], clo[4 * h + j], pack2(cj32, cj32));
-          }
-        }
-      }
-      const uint64_t r = f2_add(hi, lo);
-      out[2 * h] = lo_of(r);
-      out[2 * h + 1] = hi_of(r);
-    }
-    if (g.tri && i == nn) out[1] = out[2] = out[3] = 0.f;  // Hermitian diagonal is real
-    float *dst0 = c_elem(g, ci, cj);
-    if (g.layout == QGEMM_INTERLEAVED) {
-      if (g.c_vec4)
-        *reinterpret_cast<float4 *>(dst0) = make_float4(out[0], out[1], out[2], out[3]);
-      else
-#pragma unroll
-        for (int s = 0; s < 4; ++s) dst0[s] = out[s];
+    if (r.tri && r.i == nn) o[1] = o[2] = o[3] = 0.f;
+    float *e = r.base + q * r.step;
+    // C is not read again by this kernel: the stores bypass L1
+    if (r.vec4) {
+      __stcg(reinterpret_cast<float4 *>(e), make_float4(o[0], o[1], o[2], o[3]));
     } else {
 #pragma unroll
-      for (int s = 0; s < 4; ++s) dst0[s * g.psC] = out[s];
+      for (int s = 0; s < 4; ++s) __stcg(e + s * r.cs, o[s]);
     }
   }
 }
 
-// Epilogue of one tile for one drain thread: row i, the quaternion columns
-// from nbase up to 32 or the tile's end nlim, accumulated P in packed pairs (component c of column q
-// is word q % 2 of acc[16 c + q / 2]); out = P + beta C (beta on the left)
-// in double-float with one rounding, kCBatch columns per call.
-__device__ __forceinline__ void epilogue(const GemmParams &g, int64_t i, int64_t nbase,
-                                         int64_t nlim, const uint64_t (&acc)[64]) {
-  if (i >= g.m) return;
-  if (g.tri == 2 && nbase + 31 < i) return;
+// Moves into L2 the C elements that acc_init_beta_c will read (issued for the
+// next tile while this one still runs, so those loads hit L2).
+__device__ __forceinline__ void prefetch_c(const CRow &r) {
+  if (r.beta_mode == 0) return;
+#pragma unroll 4
+  for (int q = 0; q < 32; ++q) {
+    if (q >= r.nq) break;
+    const float *e = r.base + q * r.step;
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(e));
+    if (!r.vec4) {
 #pragma unroll
-  for (int qb = 0; qb < 32; qb += kCBatch) {
-    if (nbase + qb >= nlim) break;
-    // the next batch's C moves into L1 while this batch computes
-    if (qb + kCBatch < 32) prefetch_c_l1(g, i, nbase + qb + kCBatch, nlim);
-    CBatch cur;
-    load_c_batch(g, i, nbase + qb, nlim, cur);
-    PBatch pb;
-#pragma unroll
-    for (int u = 0; u < kCBatch; ++u)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) pb.p[u][c] = acc_at(acc, c, qb + u);
-    epilogue_batch(g, i, nbase + qb, nlim, pb, cur);
+      for (int s = 1; s < 4; ++s) asm volatile("prefetch.global.L2 [%0];" ::"l"(e + s * r.cs));
+    }
   }
 }
 
@@ -1085,6 +1068,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const TileInfo ti = tile_info<GROUPED>(t, e, single, &tmA, &tmB, probs);
         if (ti.skip) continue;
         const CUtensorMap *mA = ti.mA, *mB = ti.mB;
+        if (GROUPED) {
+          tma_prefetch_desc(mA);
+          tma_prefetch_desc(mB);
+        }
         const int mt = ti.mt, n0 = ti.n0;
         const uint32_t bytes = static_cast<uint32_t>(ti.pa) * TERMS * kAPlaneBytes +
                                static_cast<uint32_t>(ti.pb) * TERMS * kBPlaneBytes;
@@ -1165,6 +1152,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t lane_base = static_cast<uint32_t>(32 * quad) << 16;
     uint32_t c_run = 0;
     bool ok = true;
+    float4 pre[kCPre];      // first C columns of the next tile, loaded before the stores
+    bool have_pre = false;
     int4 e_next = make_int4(0, 0, 0, 0);
     if (GROUPED && static_cast<int>(blockIdx.x) < ntiles) e_next = tiles[blockIdx.x];
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -1181,18 +1170,26 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool mine = 32 * half < ti.ncols;          // this warp's columns hold data
       const int nacc = ti.pa > ti.pb ? ti.pa : ti.pb;  // components the MMAs write
       const bool split_k = !GROUPED && single.ksplit > 1;  // grouped problems never split K
-      // C moves into L2 two chunks before the epilogue reads it (earlier, the
-      // streaming operands of the other tiles evict it again)
-      const int pf_chunk = nch > 2 ? nch - 2 : 0;
-      if (!split_k && mine && nch == 0)
-        prefetch_c(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane, nbase, nlim);
+      const int64_t row = static_cast<int64_t>(mt) * BM + 32 * quad + lane;
+      // beta C is added here unless K is split (the reduction kernel adds it)
+      const CRow cr = c_row(*g, row, nbase, mine ? nlim : nbase, !split_k);
+      // the next tile's C moves into L2 four chunks before this tile ends
+      // (much earlier, the streaming operands of the other tiles evict it)
+      const int pf_chunk = nch > 4 ? nch - 4 : 0;
+      const int t_next = t + static_cast<int>(gridDim.x);
       uint64_t acc[64];  // packed pairs: component c, columns 2i, 2i + 1 in acc[16 c + i]
-#pragma unroll
-      for (int i = 0; i < 64; ++i) acc[i] = 0ull;
+      acc_init_beta_c(cr, acc, pre, have_pre);
+      have_pre = false;
       for (int ch = 0; ch < nch; ++ch, ++c_run) {
         const int b = c_run & 1;
-        if (ch == pf_chunk && !split_k && mine)
-          prefetch_c(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane, nbase, nlim);
+        if (ch == pf_chunk && t_next < ntiles) {
+          const TileInfo tn = tile_info<GROUPED>(t_next, e_next, single, &tmA, &tmB, probs);
+          const int64_t nb2 = static_cast<int64_t>(tn.n0) + 32 * half;
+          if (!tn.skip && 32 * half < tn.ncols)
+            prefetch_c(c_row(*tn.g, static_cast<int64_t>(tn.mt) * BM + 32 * quad + lane, nb2,
+                             min(tn.g->n, static_cast<int64_t>(tn.n0) + tn.ncols),
+                             !split_k));
+        }
         if (!wait_phase(&ctl->accfull[b], (c_run >> 1) & 1, limit_ns, ctl)) {
           set_abort<Err>(ctl);
           ok = false;
@@ -1236,11 +1233,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(&ctl->accempty[b]);
       }
       if (!ok) break;
+      // the first columns go out, then the next tile's first C loads are
+      // issued (into the registers those columns held), then the rest
+      if (mine && !split_k) store_acc<0, kCPre>(cr, acc);
       if (!mine) continue;
       if (split_k)
-        store_partial(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane, nbase, z, acc);
+        store_partial(*g, row, nbase, z, acc);
       else
-        epilogue(*g, static_cast<int64_t>(mt) * BM + 32 * quad + lane, nbase, nlim, acc);
+        store_acc<kCPre, 32>(cr, acc);
     }
   }
 
