@@ -340,15 +340,9 @@ __device__ __forceinline__ void tmem_st_wait() {
 
 // ------------------------------------------------ double-float helpers ---
 // Error-free transformations on FP32 (Knuth's TwoSum; the product error by
-// one FMA).  The _rn intrinsics are never contracted or reassociated.
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-  s = __fadd_rn(a, b);
-  const float bp = __fsub_rn(s, a);
-  const float ap = __fsub_rn(s, bp);
-  e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
-}
-// The same on two FP32 values at once (packed .f32x2 arithmetic: half the
-// instructions).  A pair is a 64-bit register: low word first.
+// one FMA), on two values at once: packed .f32x2 arithmetic, whose
+// instructions round to nearest and are never contracted or reassociated.  A
+// pair is a 64-bit register: low word first.
 __device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
   uint64_t r;
   asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
@@ -383,25 +377,25 @@ __device__ __forceinline__ float hi_of(uint64_t x) {
   return __uint_as_float(static_cast<uint32_t>(x >> 32));
 }
 
-// (hi, lo) += (sh + sl) x: the product sh x exactly (value and FMA error),
-// sl x in FP32, the sum by TwoSum; lo collects the small parts.
-__device__ __forceinline__ void df_fma(float &hi, float &lo, float sh, float sl, float x) {
-  const float p = __fmul_rn(sh, x);
-  float e = __fmaf_rn(sh, x, -p);
-  e = __fmaf_rn(sl, x, e);
-  float s, e2;
-  two_sum(hi, p, s, e2);
-  hi = s;
-  lo = __fadd_rn(lo, __fadd_rn(e, e2));
+// Two FP32 values as BF16 (round to nearest even) in one 32-bit word: the
+// low word's value in the low half (the lower address once stored).
+__device__ __forceinline__ uint32_t bf16x2_rn(uint64_t x) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi_of(x)), "f"(lo_of(x)));
+  return r;
 }
-// Three BF16 terms of the double-float value hi + lo (round to nearest):
-// hi - t0 is exact in FP32, so the residual after three terms is below
-// 2^-27 |hi|.
-__device__ __forceinline__ void split3_df(float hi, float lo, __nv_bfloat16 (&t)[3]) {
-  t[0] = __float2bfloat16_rn(hi);
-  const float r1 = __fadd_rn(__fsub_rn(hi, __bfloat162float(t[0])), lo);
-  t[1] = __float2bfloat16_rn(r1);
-  t[2] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(t[1])));
+// The two BF16 values of a word back as an FP32 pair (exact).
+__device__ __forceinline__ uint64_t bf16x2_to_f2(uint32_t t) {
+  return pack2(t << 16, t & 0xffff0000u);
+}
+// Three BF16 terms of each of two double-float values hi + lo (round to
+// nearest), as three words of two BF16 each: hi - t0 is exact in FP32, so
+// the residual after three terms is below 2^-27 |hi|.
+__device__ __forceinline__ void split3_df2(uint64_t hi, uint64_t lo, uint32_t (&t)[3]) {
+  t[0] = bf16x2_rn(hi);
+  const uint64_t r1 = f2_add(f2_sub(hi, bf16x2_to_f2(t[0])), lo);
+  t[1] = bf16x2_rn(r1);
+  t[2] = bf16x2_rn(f2_sub(r1, bf16x2_to_f2(t[1])));
 }
 
 // ----------------------------------------------------------- pre-pass ---
@@ -412,9 +406,10 @@ __device__ __forceinline__ void split3_df(float hi, float lo, __nv_bfloat16 (&t)
 // grouped path turned around), split into three BF16 terms and written as
 // K-major planes:
 //   out[((t * planes + c) * rows + r) * kp + kappa] = term t of (s x)^c.
-// Columns kappa >= kq are not written (the tensor maps end at kq and read
-// zeros beyond).  An operand stores `width` components per element; the
-// others read as zero.
+// The GEMM never reads columns kappa >= kq (its tensor maps end at kq and
+// read zeros beyond); a thread writes two consecutive columns, so an odd kq
+// gets a zero written at kq, inside the pitch kp.  An operand stores `width`
+// components per element; the others read as zero.
 enum { kScaleNone = 0, kScaleReal = 1, kScaleLeft = 2, kScaleRight = 3 };
 struct PrepArgs {
   const float *X;
@@ -448,33 +443,47 @@ __device__ __forceinline__ float4 load_elem(const PrepArgs &p, int64_t sr, int64
   return make_float4(v[0], v[1], v[2], v[3]);
 }
 
-// (hi, lo)^c of s x (kScaleLeft), x s (kScaleRight) or s0 x (kScaleReal).
-__device__ __forceinline__ void scale_df(const PrepArgs &p, const float (&x)[4], float (&hi)[4],
-                                         float (&lo)[4]) {
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    hi[c] = 0.f;
-    lo[c] = 0.f;
-  }
-  if (p.smode == kScaleReal) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) df_fma(hi[c], lo[c], p.s_hi[0], p.s_lo[0], x[c]);
+// Component c of s x (A side: s on the left) or x s (B side: on the right)
+// in double-float, for two elements at once: x[j] holds component j of both
+// (packed .f32x2 pairs).  Every product of an s word and x is formed without
+// error by FMA and the four products are summed by TwoSum.
+template <bool RIGHT>
+__device__ __forceinline__ void scale_df2(const PrepArgs &p, int c, const uint64_t (&x)[4],
+                                          uint64_t &hi, uint64_t &lo) {
+  if (p.smode == kScaleNone) {
+    hi = x[c];
+    lo = 0ull;
     return;
   }
-  const bool left = p.smode == kScaleLeft;
+  const bool real = p.smode == kScaleReal;
+  hi = lo = 0ull;
 #pragma unroll
-  for (int c = 0; c < 4; ++c)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int q = c ^ j;  // scalar component q meets x^j
-      const bool neg = left ? basis_sign(q, j) < 0 : basis_sign(j, q) < 0;
-      df_fma(hi[c], lo[c], neg ? -p.s_hi[q] : p.s_hi[q], neg ? -p.s_lo[q] : p.s_lo[q], x[j]);
+  for (int j = 0; j < 4; ++j) {
+    const int q = c ^ j;  // scalar component q meets x^j
+    if (real && q != 0) continue;
+    const bool neg = RIGHT ? basis_sign(j, q) < 0 : basis_sign(q, j) < 0;
+    const uint32_t sh = __float_as_uint(neg ? -p.s_hi[q] : p.s_hi[q]);
+    const uint32_t sl = __float_as_uint(neg ? -p.s_lo[q] : p.s_lo[q]);
+    const uint64_t kh = pack2(sh, sh), kl = pack2(sl, sl);
+    const uint64_t pr = f2_mul(kh, x[j]);
+    uint64_t e = f2_fma(kh, x[j], f2_neg(pr));
+    e = f2_fma(kl, x[j], e);
+    if (real || j == 0) {  // the first (a real s: the only) product
+      hi = pr;
+      lo = e;
+    } else {
+      uint64_t sum, e2;
+      two_sum2(hi, pr, sum, e2);
+      hi = sum;
+      lo = f2_add(lo, f2_add(e, e2));
     }
+  }
 }
 
-template <bool IS_B>
-__device__ __forceinline__ void prep_tile(const PrepArgs &p, int64_t rt, int64_t kt,
-                                          float4 (*tile)[33]) {
+// Phase 1 of a tile: element (r, kappa) of the tile into tile[kappa][r]
+// (zeros outside the matrix), read along the stored contiguous index.
+__device__ __forceinline__ void prep_tile_load(const PrepArgs &p, int64_t rt, int64_t kt,
+                                               float4 (*tile)[33]) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   const int64_t r0 = rt * 32, k0 = kt * 32;
 #pragma unroll
@@ -484,45 +493,61 @@ __device__ __forceinline__ void prep_tile(const PrepArgs &p, int64_t rt, int64_t
     const int kk = p.row_contig ? b : a;
     const int64_t r = r0 + rr, kq = k0 + kk;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (r < p.rows && kq < p.kq) {
-      v = load_elem(p, p.row_contig ? r : kq, p.row_contig ? kq : r);
-      if (p.conj) {
-        v.y = -v.y;
-        v.z = -v.z;
-        v.w = -v.w;
-      }
-    }
+    if (r < p.rows && kq < p.kq) v = load_elem(p, p.row_contig ? r : kq, p.row_contig ? kq : r);
     tile[kk][rr] = v;
   }
-  __syncthreads();
+}
+
+// Phase 2 of a tile (after phase 1 and a barrier): conjugation, scaling,
+// split and the K-major stores.
+template <bool IS_B>
+__device__ __forceinline__ void prep_tile_split(const PrepArgs &p, int64_t rt, int64_t kt,
+                                                float4 (*tile)[33]) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t r0 = rt * 32, k0 = kt * 32;
+  // each thread: columns kappa, kappa + 1 of two rows, every step on the pair
+  // (one packed instruction, one 4-byte store of two BF16 per term and plane)
   const int64_t plane_stride = p.rows * p.kp;
+  const int kk = 2 * (tx & 15);
+  const int64_t kq = k0 + kk;
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    const int kk = tx, rr = ty + 8 * s;
-    const int64_t r = r0 + rr, kq = k0 + kk;
+  for (int s = 0; s < 2; ++s) {
+    const int rr = (tx >> 4) + 2 * ty + 16 * s;
+    const int64_t r = r0 + rr;
     if (r >= p.rows || kq >= p.kq) continue;
-    const float4 v = tile[kk][rr];
-    const float x[4] = {v.x, v.y, v.z, v.w};
-    float hi[4], lo[4];
-    if (p.smode == kScaleNone) {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        hi[c] = x[c];
-        lo[c] = 0.f;
-      }
-    } else {
-      scale_df(p, x, hi, lo);
+    const float4 v0 = tile[kk][rr], v1 = tile[kk + 1][rr];
+    uint64_t x[4] = {pack2(__float_as_uint(v0.x), __float_as_uint(v1.x)),
+                     pack2(__float_as_uint(v0.y), __float_as_uint(v1.y)),
+                     pack2(__float_as_uint(v0.z), __float_as_uint(v1.z)),
+                     pack2(__float_as_uint(v0.w), __float_as_uint(v1.w))};
+    if (p.conj) {
+      x[1] = f2_neg(x[1]);
+      x[2] = f2_neg(x[2]);
+      x[3] = f2_neg(x[3]);
     }
-    __nv_bfloat16 *dst = p.out + r * p.kp + kq;
+    // kp is even and kq even: 4-byte aligned
+    uint32_t *dst = reinterpret_cast<uint32_t *>(p.out + r * p.kp + kq);
+    const int64_t wstride = plane_stride / 2;  // in words of two BF16
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       if (c >= p.planes) break;
-      __nv_bfloat16 t[3];
-      split3_df(hi[c], lo[c], t);
+      uint64_t hi, lo;
+      scale_df2<IS_B>(p, c, x, hi, lo);
+      uint32_t t[3];
+      split3_df2(hi, lo, t);
 #pragma unroll
-      for (int tt = 0; tt < TERMS; ++tt) dst[(tt * p.planes + c) * plane_stride] = t[tt];
+      for (int tt = 0; tt < TERMS; ++tt) dst[(tt * p.planes + c) * wstride] = t[tt];
     }
   }
+}
+
+// One tile, both phases (a CTA per tile).
+template <bool IS_B>
+__device__ __forceinline__ void prep_tile(const PrepArgs &p, int64_t rt, int64_t kt,
+                                          float4 (*tile)[33]) {
+  prep_tile_load(p, rt, kt, tile);
+  __syncthreads();
+  prep_tile_split<IS_B>(p, rt, kt, tile);
 }
 
 // --------------------------------------------------------- GEMM params ---
@@ -755,10 +780,6 @@ __device__ __forceinline__ CRow c_row(const GemmParams &g, int64_t i, int64_t nb
   return r;
 }
 
-// C columns of the next tile that a drain thread loads before it stores the
-// current tile, so that their latency passes while the stores go out.
-constexpr int kCPre = 8;
-
 // C of columns [q0, q0 + NQ) of r (zeros outside C, and when beta C is not
 // added here).  The loads bypass L1: its few KB beside the operand ring would
 // hold only a handful of them in flight.
@@ -815,30 +836,24 @@ __device__ __forceinline__ void beta_c_into(const CRow &r, int q0, const float4 
 
 // Starts the accumulation of a tile at beta C (zero where C is not read), so
 // that C enters the compensated sum like one more chunk and the tile's end
-// only stores.  pre holds the first kCPre columns when have_pre (loaded
-// before the previous tile's stores); the other loads are all issued before
-// their first use and wait on memory while the tile's first chunk runs on
-// the tensor cores.
-__device__ __forceinline__ void acc_init_beta_c(const CRow &r, uint64_t (&acc)[64],
-                                                const float4 (&pre)[kCPre], bool have_pre) {
+// only stores.  The loads go out in batches of 8, 12 and 12 columns and wait
+// on memory while the tile's first chunk runs on the tensor cores.
+__device__ __forceinline__ void acc_init_beta_c(const CRow &r, uint64_t (&acc)[64]) {
   if (r.beta_mode == 0) {
 #pragma unroll
     for (int i = 0; i < 64; ++i) acc[i] = 0ull;
     return;
   }
-  if (have_pre) {
-    beta_c_into<kCPre>(r, 0, pre, acc);
-  } else {
-    float4 first[kCPre];
-    load_c<kCPre>(r, 0, first);
-    beta_c_into<kCPre>(r, 0, first, acc);
+  {
+    float4 first[8];
+    load_c<8>(r, 0, first);
+    beta_c_into<8>(r, 0, first, acc);
   }
-  constexpr int kHalf = (32 - kCPre) / 2;
-  float4 rest[kHalf];
-  load_c<kHalf>(r, kCPre, rest);
-  beta_c_into<kHalf>(r, kCPre, rest, acc);
-  load_c<kHalf>(r, kCPre + kHalf, rest);
-  beta_c_into<kHalf>(r, kCPre + kHalf, rest, acc);
+  float4 rest[12];
+  load_c<12>(r, 8, rest);
+  beta_c_into<12>(r, 8, rest, acc);
+  load_c<12>(r, 20, rest);
+  beta_c_into<12>(r, 20, rest, acc);
 }
 
 __device__ __forceinline__ float acc_at(const uint64_t (&acc)[64], int c, int q) {
@@ -1152,8 +1167,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t lane_base = static_cast<uint32_t>(32 * quad) << 16;
     uint32_t c_run = 0;
     bool ok = true;
-    float4 pre[kCPre];      // first C columns of the next tile, loaded before the stores
-    bool have_pre = false;
     int4 e_next = make_int4(0, 0, 0, 0);
     if (GROUPED && static_cast<int>(blockIdx.x) < ntiles) e_next = tiles[blockIdx.x];
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -1178,8 +1191,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int pf_chunk = nch > 4 ? nch - 4 : 0;
       const int t_next = t + static_cast<int>(gridDim.x);
       uint64_t acc[64];  // packed pairs: component c, columns 2i, 2i + 1 in acc[16 c + i]
-      acc_init_beta_c(cr, acc, pre, have_pre);
-      have_pre = false;
+      acc_init_beta_c(cr, acc);
       for (int ch = 0; ch < nch; ++ch, ++c_run) {
         const int b = c_run & 1;
         if (ch == pf_chunk && t_next < ntiles) {
@@ -1233,14 +1245,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(&ctl->accempty[b]);
       }
       if (!ok) break;
-      // the first columns go out, then the next tile's first C loads are
-      // issued (into the registers those columns held), then the rest
-      if (mine && !split_k) store_acc<0, kCPre>(cr, acc);
+      // stored in two parts, the first before the test of `mine`: with one
+      // store loop after it, the compiler kept more of the accumulator live
+      // and spilled (ptxas -v)
+      if (mine && !split_k) store_acc<0, 8>(cr, acc);
       if (!mine) continue;
       if (split_k)
         store_partial(*g, row, nbase, z, acc);
       else
-        store_acc<kCPre, 32>(cr, acc);
+        store_acc<8, 32>(cr, acc);
     }
   }
 
