@@ -321,9 +321,14 @@ void fp64_arm_fault(int stage, uint64_t limit_ns) {
 }
 
 int launch_fp64_gemm_ws(const GemmDesc &d, void *ws, size_t ws_bytes, cudaStream_t stream) {
+  const int debug_skip = g_fp64_debug_skip.exchange(0);
+  // a plain product that fills the GPU many times over runs on the FP64 FMA
+  // pipe, the faster of GB300's two FP64 pipes (fp64_dfma.cu); an armed fault
+  // (a DMMA-kernel test hook) keeps the DMMA kernel
+  if (!debug_skip && fp64_dfma_eligible(d, device_sms())) return launch_fp64_dfma(d, stream);
   Fp64Args a{};
   a.op = fp64_operands(d);
-  a.op.debug_skip = g_fp64_debug_skip.exchange(0);
+  a.op.debug_skip = debug_skip;
   a.limit_ns = a.op.debug_skip ? g_fp64_debug_limit.load() : wait_limit_ns();
   // K split when it pays and the caller's workspace holds the partials
   int ks = fp64_ksplit(d, device_sms());

@@ -58,6 +58,11 @@ EncodeTiledFn encode_tiled_fn();
 int launch_status();
 int record_cuda_error(cudaError_t e);
 
+// FP64 product on the FP64 FMA pipe (fp64_dfma.cu): whether a product takes
+// it, and its launch.
+bool fp64_dfma_eligible(const GemmDesc &d, int sms);
+int launch_fp64_dfma(const GemmDesc &d, cudaStream_t stream);
+
 // Device wait limit for bounded spins (env QGEMM_WAIT_LIMIT_MS, default 2000).
 uint64_t wait_limit_ns();
 
