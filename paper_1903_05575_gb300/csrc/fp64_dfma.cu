@@ -30,6 +30,11 @@ constexpr int kTQ = 32;  // quaternion rows / columns of C per CTA
 constexpr int kKQ = 16;  // quaternion kappa per shared-memory step
 constexpr int kGroupM = 16;  // row tiles per raster group
 
+// One quaternion in registers or shared memory.
+struct alignas(32) Qd {
+  double x, y, z, w;
+};
+
 struct DfmaArgs {
   const double *A, *B;
   double *C;
@@ -44,18 +49,18 @@ struct DfmaArgs {
 };
 
 // Element (r, c) of a STORED operand with four components.
-__device__ __forceinline__ double4 load_q(const double *X, int64_t ld, int64_t ps, int planes,
+__device__ __forceinline__ Qd load_q(const double *X, int64_t ld, int64_t ps, int planes,
                                           int64_t r, int64_t c) {
   if (!planes) {
     const double *e = X + 4 * (r + c * ld);
-    return make_double4(e[0], e[1], e[2], e[3]);
+    return Qd{e[0], e[1], e[2], e[3]};
   }
   const double *e = X + r + c * ld;
-  return make_double4(e[0], e[ps], e[2 * ps], e[3 * ps]);
+  return Qd{e[0], e[ps], e[2 * ps], e[3 * ps]};
 }
 
 // acc += a b (Hamilton product, signs as FMA negations).
-__device__ __forceinline__ void qmac(double (&acc)[4], const double4 &a, const double4 &b) {
+__device__ __forceinline__ void qmac(double (&acc)[4], const Qd &a, const Qd &b) {
   const double av[4] = {a.x, a.y, a.z, a.w};
   const double bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
@@ -80,8 +85,8 @@ __device__ __forceinline__ void qmac_left(double (&out)[4], const double (&s)[4]
 }
 
 __global__ void __launch_bounds__(256, 2) fp64_dfma_kernel(const DfmaArgs a) {
-  __shared__ double4 As[kKQ][kTQ];  // op(A)(i0 + i, k0 + kappa) at As[kappa][i]
-  __shared__ double4 Bs[kKQ][kTQ];  // op(B)(k0 + kappa, n0 + n) at Bs[kappa][n]
+  __shared__ Qd As[kKQ][kTQ];  // op(A)(i0 + i, k0 + kappa) at As[kappa][i]
+  __shared__ Qd Bs[kKQ][kTQ];  // op(B)(k0 + kappa, n0 + n) at Bs[kappa][n]
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   // raster: groups of kGroupM row tiles walked column by column, so the CTAs
@@ -112,7 +117,7 @@ __global__ void __launch_bounds__(256, 2) fp64_dfma_kernel(const DfmaArgs a) {
         const int i = a.transA ? (e >> 4) : (e & 31);
         const int kk = a.transA ? (e & 15) : (e >> 5);
         const int64_t gi = i0 + i, gk = k0 + kk;
-        double4 v = make_double4(0.0, 0.0, 0.0, 0.0);
+        Qd v = Qd{0.0, 0.0, 0.0, 0.0};
         if (gi < a.m && gk < a.k)
           v = a.transA ? load_q(a.A, a.lda, a.psA, a.planes, gk, gi)
                        : load_q(a.A, a.lda, a.psA, a.planes, gi, gk);
@@ -128,7 +133,7 @@ __global__ void __launch_bounds__(256, 2) fp64_dfma_kernel(const DfmaArgs a) {
         const int nn = a.transB ? (e & 31) : (e >> 4);
         const int kk = a.transB ? (e >> 5) : (e & 15);
         const int64_t gn = n0 + nn, gk = k0 + kk;
-        double4 v = make_double4(0.0, 0.0, 0.0, 0.0);
+        Qd v = Qd{0.0, 0.0, 0.0, 0.0};
         if (gn < a.n && gk < a.k)
           v = a.transB ? load_q(a.B, a.ldb, a.psB, a.planes, gn, gk)
                        : load_q(a.B, a.ldb, a.psB, a.planes, gk, gn);
@@ -143,8 +148,8 @@ __global__ void __launch_bounds__(256, 2) fp64_dfma_kernel(const DfmaArgs a) {
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < kKQ; ++kk) {
-      const double4 a0 = As[kk][2 * ty], a1 = As[kk][2 * ty + 1];
-      const double4 b0 = Bs[kk][2 * tx], b1 = Bs[kk][2 * tx + 1];
+      const Qd a0 = As[kk][2 * ty], a1 = As[kk][2 * ty + 1];
+      const Qd b0 = Bs[kk][2 * tx], b1 = Bs[kk][2 * tx + 1];
       qmac(acc[0][0], a0, b0);
       qmac(acc[0][1], a0, b1);
       qmac(acc[1][0], a1, b0);
@@ -176,13 +181,29 @@ __global__ void __launch_bounds__(256, 2) fp64_dfma_kernel(const DfmaArgs a) {
 }  // namespace
 
 // The DFMA kernel serves a plain product of quaternion operands whose grid
-// fills the GPU many times over (32 x 32 tiles; at least 16 waves of the two
-// CTAs per SM, so the partial last wave costs little).
+// of 32 x 32 tiles fills the GPU: at least 8 tiles per SM, and the waves of
+// the CTAs that fit at once at least 90 % full (the DMMA kernel's 16 x 16
+// tiles fill smaller or ragged grids better).
 bool fp64_dfma_eligible(const GemmDesc &d, int sms) {
-  if (d.tri || d.krange || d.swap || d.kwidth != 4 || d.A.width != 4 || d.B.width != 4)
+  if (d.tri || d.krange || d.swap || d.kwidth != 4 || d.A.width != 4 || d.B.width != 4 ||
+      d.k <= 0)
     return false;
   const int64_t tiles = ((d.m + kTQ - 1) / kTQ) * ((d.n + kTQ - 1) / kTQ);
-  return tiles >= 32LL * sms && d.k > 0;
+  if (tiles < 8LL * sms) return false;
+  static int per_sm = 0;  // resident CTAs per SM (fixed by the kernel's resources)
+  if (per_sm == 0) {
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, fp64_dfma_kernel, 256, 0) !=
+            cudaSuccess ||
+        v <= 0) {
+      cudaGetLastError();
+      v = 2;
+    }
+    per_sm = v;
+  }
+  const int64_t slots = static_cast<int64_t>(per_sm) * sms;
+  const int64_t waves = (tiles + slots - 1) / slots;
+  return static_cast<double>(tiles) >= 0.9 * static_cast<double>(waves * slots);
 }
 
 int launch_fp64_dfma(const GemmDesc &d, cudaStream_t stream) {

@@ -1,5 +1,6 @@
 """FP64 products large enough for the FP64 FMA-pipe kernel (fp64_dfma.cu:
-32 x 32-quaternion tiles, taken when the grid has at least 32 tiles per SM)
+32 x 32-quaternion tiles, taken when the grid has at least 8 tiles per SM
+and its waves are at least 90 % full)
 against the FP64 oracle, through the C ABI.
 
 Shapes are ragged in every dimension (2049 x 2433 x 37: 65 x 77 tiles) with
