@@ -26,8 +26,11 @@
  *       interleaved layout.
  *
  * Precision:
- *   QGEMM_FP64:            double data; products on FP64 tensor cores (DMMA),
- *                          FP64 accumulation and epilogue.  Needs no
+ *   QGEMM_FP64:            double data; FP64 products, accumulation and
+ *                          epilogue: a product whose 32 x 32-quaternion tiles
+ *                          fill the GPU runs on the FP64 FMA pipe (the faster
+ *                          FP64 pipe of GB300), the others on the FP64 tensor
+ *                          cores (DMMA).  Needs no
  *                          workspace; given one of qgemm_workspace_bytes()
  *                          bytes, a product whose C is too small to fill the
  *                          GPU (fewer than 8 waves of 16 x 16 quaternion
@@ -39,10 +42,12 @@
  *   QGEMM_FP32_SPLIT_BF16: float data; each operand is split into three BF16
  *                          terms (hi, mid, lo), the six leading term products
  *                          run on the BF16 tensor cores (tcgen05) with FP32
- *                          accumulation in tensor memory, drained in K-chunks
- *                          into a higher-precision accumulator; alpha and beta
- *                          are applied in FP64 and the result is rounded once
- *                          to float.  Needs a workspace (qgemm_workspace_bytes;
+ *                          accumulation in tensor memory, added every 16
+ *                          kappa to a register sum by compensated (TwoSum)
+ *                          addition; alpha scales op(A) in double-float before
+ *                          the split and beta C (FP32 products) is the sum's
+ *                          starting value; one final rounding to float.
+ *                          Needs a workspace (qgemm_workspace_bytes;
  *                          beyond its minimum, the size reported lets a
  *                          product with few tiles of C and a long k split K
  *                          across CTAs, as QGEMM_FP64).
